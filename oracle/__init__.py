@@ -1,0 +1,211 @@
+"""CPU oracle for the CSWENO-limited RKDG method -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It wraps ``oracle.c`` (plain FP64 C, single-threaded,
+compiled with ``-ffp-contract=off`` so that no fused multiply-add changes its rounding)
+through ctypes and shares nothing with the CUDA library.
+
+Modal arrays use the library's public layout ``[cell][var][mode]`` with
+``cell = iy * nx + ix``; 2D modes are ordered by total degree, then by the y-degree.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against
+the paper's printed constants (Sec. 3, P2 tables and smoothness indicators), closed
+forms, invariants or brute force.  The P3 limiter constants have no printed values;
+they are pinned by an independent derivation and by polynomial reproduction only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PDE_BURGERS, PDE_EULER = 0, 1
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` beside it (plain gcc, no FMA contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", _LIB_PATH + ".tmp", _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("pde", ctypes.c_int), ("N", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int),
+                ("xL", ctypes.c_double), ("xR", ctypes.c_double),
+                ("yL", ctypes.c_double), ("yR", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+_I = ctypes.POINTER(ctypes.c_int)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = ctypes.CDLL(build())
+            M = ctypes.POINTER(_Mesh)
+            l.or_rhs.argtypes = [M, _D, _D]
+            l.or_rk_stage.argtypes = [M, ctypes.c_int, ctypes.c_double, _D, _D, _D]
+            l.or_flag_tvb.argtypes = [M, _D, ctypes.c_double, _U8, _L]
+            l.or_flag_tvb.restype = ctypes.c_long
+            l.or_csweno_limit.argtypes = [M, _D, _U8, _D, ctypes.c_double]
+            l.or_step.argtypes = [M, ctypes.c_double, _D, ctypes.c_double, ctypes.c_int, ctypes.c_double, _L]
+            l.or_step.restype = ctypes.c_long
+            l.or_max_wavespeed.argtypes = [M, _D, _D]
+            l.or_project_ic.argtypes = [M, ctypes.c_int, _D, _D]
+            l.or_euler_eigen.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D, _D]
+            l.or_weno_export.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _I, _D]
+            l.or_dg_export.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+            _lib = l
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def nmodes(dim: int, N: int) -> int:
+    return N + 1 if dim == 1 else (N + 1) * (N + 2) // 2
+
+
+def nvars(dim: int, pde: int) -> int:
+    return 1 if pde == PDE_BURGERS else (3 if dim == 1 else 4)
+
+
+def mode_ab(dim: int, N: int):
+    """(a, b) degrees of every mode in storage order."""
+    if dim == 1:
+        return [(n, 0) for n in range(N + 1)]
+    out = []
+    for d in range(N + 1):
+        for b in range(d + 1):
+            out.append((d - b, b))
+    return out
+
+
+class Mesh:
+    """One mesh instance: dim 1 or 2, pde, degree N, nx x ny cells on the box, bc."""
+
+    def __init__(self, dim, pde, N, nx, ny=1, box=(0.0, 1.0, 0.0, 1.0), bc=BC_PERIODIC, gamma=1.4):
+        if dim == 1:
+            ny = 1
+        self.dim, self.pde, self.N, self.nx, self.ny, self.bc = dim, pde, N, nx, ny, bc
+        self.box = tuple(float(b) for b in box)
+        self.gamma = float(gamma)
+        self._m = _Mesh(dim, pde, N, nx, ny, bc, *self.box, self.gamma)
+        self.nv = nvars(dim, pde)
+        self.np = nmodes(dim, N)
+        self.shape = (nx * ny, self.nv, self.np)
+
+    @property
+    def h(self):
+        xL, xR, yL, yR = self.box
+        return ((xR - xL) / self.nx, (yR - yL) / self.ny if self.dim == 2 else None)
+
+    def _ref(self):
+        return ctypes.byref(self._m)
+
+    def zeros(self):
+        return np.zeros(self.shape, dtype=np.float64)
+
+    def _chk(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.size == self.nx * self.ny * self.nv * self.np
+        return u.reshape(self.shape)
+
+    def rhs(self, u):
+        u = self._chk(u)
+        L = self.zeros()
+        lib().or_rhs(self._ref(), _dp(u), _dp(L))
+        return L
+
+    def rk_stage(self, stage, dt, un, us):
+        un, us = self._chk(un), self._chk(us)
+        out = self.zeros()
+        lib().or_rk_stage(self._ref(), stage, dt, _dp(un), _dp(us), _dp(out))
+        return out
+
+    def flag_tvb(self, u, M=0.01):
+        u = self._chk(u)
+        fl = np.zeros(self.nx * self.ny, dtype=np.uint8)
+        near = ctypes.c_long(0)
+        n = lib().or_flag_tvb(self._ref(), _dp(u), M, fl.ctypes.data_as(_U8), ctypes.byref(near))
+        return fl, int(n), int(near.value)
+
+    def limit(self, u, flags, eps=1e-6):
+        u = self._chk(u)
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        out = self.zeros()
+        lib().or_csweno_limit(self._ref(), _dp(u), fl.ctypes.data_as(_U8), _dp(out), eps)
+        return out
+
+    def step(self, u, dt, M=0.01, limit=True, eps=1e-6):
+        """One SSP-RK3 step, limiter after each stage. Returns (u_new, n_flagged, n_near)."""
+        u = self._chk(u).copy()
+        near = ctypes.c_long(0)
+        nf = lib().or_step(self._ref(), dt, _dp(u), M, int(limit), eps, ctypes.byref(near))
+        return u, int(nf), int(near.value)
+
+    def max_wavespeed(self, u):
+        u = self._chk(u)
+        out = np.zeros(2)
+        lib().or_max_wavespeed(self._ref(), _dp(u), _dp(out))
+        return out
+
+    def project_ic(self, kind, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        out = self.zeros()
+        lib().or_project_ic(self._ref(), kind, _dp(p), _dp(out))
+        return out
+
+
+def euler_eigen(dim, gamma, direction, u):
+    nv = 3 if dim == 1 else 4
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    R = np.zeros((nv, nv))
+    L = np.zeros((nv, nv))
+    lib().or_euler_eigen(dim, gamma, direction, _dp(u), _dp(R), _dp(L))
+    return R, L
+
+
+def weno_tables(N: int):
+    """The CSWENO tables the oracle derived for degree N (Sec. 3, Steps 1-4)."""
+    ns = 2 * N + 1
+    ng = 2 if N == 1 else 4
+    pt, wt = np.zeros(ng), np.zeros(ng)
+    C = np.zeros((N + 1, ng, ns))
+    D = np.zeros((ng, ns))
+    gam = np.zeros((ng, N + 1))
+    B = np.zeros((N + 1, ns, ns))
+    SA = np.zeros((ns, N + 1))
+    OFF = np.zeros(ns, dtype=np.int32)
+    resid = ctypes.c_double(0)
+    lib().or_weno_export(N, _dp(pt), _dp(wt), _dp(C), _dp(D), _dp(gam), _dp(B), _dp(SA),
+                         OFF.ctypes.data_as(_I), ctypes.byref(resid))
+    return dict(pt=pt, wt=wt, C=C, D=D, gam=gam, B=B, SA=SA, OFF=OFF, resid=resid.value)
+
+
+def dg_tables(N: int, nq: int):
+    x, w = np.zeros(nq), np.zeros(nq)
+    P, dP = np.zeros((nq, N + 1)), np.zeros((nq, N + 1))
+    lib().or_dg_export(N, nq, _dp(x), _dp(w), _dp(P), _dp(dP))
+    return x, w, P, dP

@@ -1,0 +1,152 @@
+"""Seeded synthetic workloads.
+
+This module only draws random numbers and states problem parameters; it holds none of
+the method's arithmetic, so that the CUDA path and the CPU oracle can both take their
+inputs from it.  Every workload is a closed-form initial condition of the kind the
+paper's examples use (Sec. 4): a sine wave for Burgers (Examples 1, 2, 5), shock tubes
+for 1D Euler (Examples 7, 8) and four-quadrant Riemann problems for 2D Euler.
+
+Initial-condition families (``ic`` codes shared with the library's projection call):
+  0 sine:          u = p0 + p1 sin(p2 x + p3 y)
+  1 Riemann 1D:    (rho,u,p)_L = p0..p2 for x < p6, (rho,u,p)_R = p3..p5 otherwise
+  2 four quadrant: (rho,u,v,p) for x>=p16,y>=p17 (p0..3); x<p16,y>=p17 (p4..7);
+                   x<p16,y<p17 (p8..11); x>=p16,y<p17 (p12..15)
+  3 density wave:  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+SEED = 1904
+
+PDE_BURGERS, PDE_EULER = 0, 1
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+GAMMA = 1.4
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    pde: int
+    N: int
+    nx: list
+    ny: list
+    box: list            # per instance (xL, xR, yL, yR)
+    bc: int
+    ic: int
+    params: list         # per instance parameter vector
+    t_end: float
+    cfl: float = 0.1
+    tvb_M: float = 0.01
+    gamma: float = GAMMA
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_inst(self):
+        return len(self.nx)
+
+    @property
+    def nvars(self):
+        return 1 if self.pde == PDE_BURGERS else (3 if self.dim == 1 else 4)
+
+    @property
+    def nmodes(self):
+        return self.N + 1 if self.dim == 1 else (self.N + 1) * (self.N + 2) // 2
+
+    @property
+    def cells(self):
+        return int(sum(a * b for a, b in zip(self.nx, self.ny)))
+
+    @property
+    def dofs(self):
+        return self.cells * self.nvars * self.nmodes
+
+
+def burgers_1d(K: int = 160, N: int = 2, t_end: float = 1.5 / math.pi) -> Workload:
+    """1D Burgers on [-1,1], periodic, u0 = 0.5 + sin(pi x) (Example 1 rescaled by pi)."""
+    return Workload("burgers1d_p%d_k%d" % (N, K), 1, PDE_BURGERS, N, [K], [1], [(-1.0, 1.0, 0.0, 1.0)],
+                    BC_PERIODIC, IC_SINE, [[0.5, 1.0, math.pi, 0.0]], t_end)
+
+
+def shock_tube(kind: str = "sod", K: int = 800, N: int = 3, index: int = 0) -> Workload:
+    """1D Euler shock tubes on [0,1] split at x = 0.5: Sod (t=0.2), Lax (t=0.13), or the
+    seeded random tube number ``index`` (rho,p ~ U[0.1,2], u ~ U[-1,1] per side)."""
+    if kind == "sod":
+        p, t = [1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 0.5], 0.2
+    elif kind == "lax":
+        p, t = [0.445, 0.698, 3.528, 0.5, 0.0, 0.571, 0.5], 0.13
+    else:
+        r = np.random.default_rng(SEED + index)
+        rl, pl, rr, pr = r.uniform(0.1, 2.0, 4)
+        ul, ur = r.uniform(-1.0, 1.0, 2)
+        p, t = [rl, ul, pl, rr, ur, pr, 0.5], 0.1
+    return Workload("%s_tube_p%d_k%d" % (kind, N, K), 1, PDE_EULER, N, [K], [1], [(0.0, 1.0, 0.0, 1.0)],
+                    BC_OUTFLOW, IC_RIEMANN1D, [list(map(float, p))], t)
+
+
+def quadrant_states(rng) -> list:
+    """18 parameters of a four-quadrant Riemann problem split at (0.5, 0.5)."""
+    p = []
+    for _ in range(4):
+        rho, pr = rng.uniform(0.1, 2.0, 2)
+        u, v = rng.uniform(-1.0, 1.0, 2)
+        p += [float(rho), float(u), float(v), float(pr)]
+    return p + [0.5, 0.5]
+
+
+def euler_2d_quadrant(n: int = 1024, N: int = 2, seed: int = SEED) -> Workload:
+    """2D Euler four-quadrant Riemann problem on [0,1]^2, outflow, to t = 0.25."""
+    rng = np.random.default_rng(seed)
+    return Workload("euler2d_quadrant_p%d_%dx%d" % (N, n, n), 2, PDE_EULER, N, [n], [n], [(0.0, 1.0, 0.0, 1.0)],
+                    BC_OUTFLOW, IC_QUADRANT, [quadrant_states(rng)], 0.25)
+
+
+def burgers_2d_batched(n_inst: int = 64, N: int = 2, lo: int = 64, hi: int = 512, seed: int = SEED) -> Workload:
+    """Batched 2D Burgers on [-2,2]^2, periodic, u0 = 0.5 + A sin(pi (x+y)/2), A ~ U[0.5,1.5],
+    square meshes with sides log-uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    sides = [int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(n_inst)]
+    amps = rng.uniform(0.5, 1.5, n_inst)
+    return Workload("burgers2d_batched_p%d_x%d" % (N, n_inst), 2, PDE_BURGERS, N, sides, sides,
+                    [(-2.0, 2.0, -2.0, 2.0)] * n_inst, BC_PERIODIC, IC_SINE,
+                    [[0.5, float(a), math.pi / 2, math.pi / 2] for a in amps], 1.0)
+
+
+def euler_2d_batched(n_inst: int = 256, N: int = 3, lo: int = 128, hi: int = 1024, seed: int = SEED) -> Workload:
+    """Batched 2D Euler four-quadrant problems, sides log-uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    sides = [int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(n_inst)]
+    params = [quadrant_states(rng) for _ in range(n_inst)]
+    return Workload("euler2d_batched_p%d_x%d" % (N, n_inst), 2, PDE_EULER, N, sides, sides,
+                    [(0.0, 1.0, 0.0, 1.0)] * n_inst, BC_OUTFLOW, IC_QUADRANT, params, 0.25)
+
+
+def random_modes(dim: int, pde: int, N: int, ncell: int, rng, jump: float = 0.3, smooth: float = 0.05,
+                 blocks: int = 7) -> np.ndarray:
+    """Random modal states [cell][var][mode] with piecewise-constant means (jumps between
+    runs of ``blocks`` cells) and small higher modes, for parity tests.  Euler states are
+    drawn as positive density and internal energy well above the kinetic part."""
+    nv = 1 if pde == PDE_BURGERS else (3 if dim == 1 else 4)
+    npm = N + 1 if dim == 1 else (N + 1) * (N + 2) // 2
+    u = np.zeros((ncell, nv, npm))
+    nb = (ncell + blocks - 1) // blocks
+    if pde == PDE_BURGERS:
+        base = rng.uniform(-1.0, 1.0, nb).repeat(blocks)[:ncell]
+        base = base + jump * rng.uniform(-1, 1, ncell) * 0.1
+        u[:, 0, 0] = base
+    else:
+        rho = rng.uniform(0.6, 1.4, nb).repeat(blocks)[:ncell] * (1 + 0.02 * rng.uniform(-1, 1, ncell))
+        vel = rng.uniform(-0.5, 0.5, (nb, dim)).repeat(blocks, axis=0)[:ncell]
+        pr = rng.uniform(0.6, 1.4, nb).repeat(blocks)[:ncell]
+        u[:, 0, 0] = rho
+        for d in range(dim):
+            u[:, 1 + d, 0] = rho * vel[:, d]
+        u[:, nv - 1, 0] = pr / (GAMMA - 1) + 0.5 * rho * (vel ** 2).sum(axis=1)
+    for k in range(1, npm):
+        u[:, :, k] = smooth * rng.uniform(-1, 1, (ncell, nv)) * np.abs(u[:, :, 0]) / (k + 1)
+    return u
