@@ -747,11 +747,17 @@ void or_euler_eigen(int dim, double gam, int dir, const double* u, double* R, do
  * ----------------------------------------------------------------------------------*/
 static void weno_1d(const or_weno_tables* t, const double* avg, double eps, double* out) {
   int N = t->N, ns = t->ns;
+  /* Every p_i reproduces constants and Eq. (13) only involves derivatives, so beta_i and
+   * p_i - c are unchanged when the constant c is removed from all averages.  Evaluating
+   * them on the averages centred at the troubled cell's own average avoids the
+   * cancellation of O(1) terms in a quadratic form whose value is O(eps). */
+  double c = avg[N], d[OR_MAXS];
+  for (int k = 0; k < ns; ++k) d[k] = avg[k] - c;
   double beta[OR_MAXN + 1];
   for (int i = 0; i <= N; ++i) {
     double s = 0;
     for (int k = 0; k < ns; ++k)
-      for (int l = 0; l < ns; ++l) s += avg[k] * t->B[i][k][l] * avg[l];
+      for (int l = 0; l < ns; ++l) s += d[k] * t->B[i][k][l] * d[l];
     beta[i] = s;
   }
   for (int g = 0; g < t->ng; ++g) {
@@ -759,8 +765,8 @@ static void weno_1d(const or_weno_tables* t, const double* avg, double eps, doub
     int negative = 0;
     for (int i = 0; i <= N; ++i) {
       double s = 0;
-      for (int k = 0; k < ns; ++k) s += t->C[i][g][k] * avg[k];
-      p[i] = s;
+      for (int k = 0; k < ns; ++k) s += t->C[i][g][k] * d[k];
+      p[i] = c + s;
       if (t->gam[g][i] < 0) negative = 1;
     }
     if (!negative) {
