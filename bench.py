@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: 2D Euler P2 DG DOF-updates/s with the CSWENO limiter on one GB300.
+
+Workload (default): the 1024 x 1024 four-quadrant Riemann problem on [0,1]^2 (2D Euler,
+gamma = 1.4, P2 = 6 modes x 4 variables, FP64 state, outflow boundaries, seed 1904), one
+SSP-RK3 step = 3 x (stage, TVB troubled-cell flags + compaction, CSWENO limiter), replayed
+from the library's CUDA graph.  DOF-updates/s = cells * modes * vars * steps / time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own replica of the
+workload (independent problems: no collective on the data path) and the value is the sum
+over ranks ("scaling": "weak").  ``--impl reference`` times the FP64 CPU oracle on the host
+cores instead (bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_11147_gb300 import workloads as W  # noqa: E402
+
+METRIC = "2D Euler P2 DG DOF-updates/s incl. CSWENO; learned vs plain indicator"
+UNIT = "DOF-updates/s"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector) nominal; the measured value is used when present
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+def stage_flops_per_cell(dim: int, pde: int, N: int) -> int:
+    """FP64 flops of one stage of Eq. (5) for one cell, counted from the formulation the
+    stage kernel evaluates (FMA = 2, add/mul/div/sqrt = 1); halo work is not counted."""
+    assert dim == 2
+    V = 1 if pde == 0 else 4
+    NP = (N + 1) * (N + 2) // 2
+    Q = N + 1
+    ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
+    n_dx = sum(1 for a, b in ab if a >= 1)
+    n_dy = sum(1 for a, b in ab if b >= 1)
+    evalf = Q * Q * V * (2 * NP - 1)
+    flux = Q * Q * (24 if pde == 1 else 4)
+    proj = Q * Q * V * 2 * (n_dx + n_dy)
+    traces = 2 * V * (2 * NP + 2 * (N + 1) + Q * (N + 1) * 4)
+    llf_point = (57 if pde == 1 else 3 * 2 + 1 + 5)
+    llf = 2 * Q * llf_point
+    lift = V * (4 * Q + 4 * (N + 1) * Q * 2 + 2 * NP * 2)
+    rk = V * NP * 4
+    return evalf + flux + proj + traces + llf + lift + rk
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, out_path=None):
+        self.proc = None
+        self.path = out_path
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self.path:
+                with open(self.path, "w") as f:
+                    f.write("\n".join(self.lines) + "\n")
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def _oracle_sample(args):
+    """Runs the oracle on one window of the workload's initial state for `steps` steps;
+    returns (dofs * steps, seconds)."""
+    wl_name, n, y0, x0, win, steps, dt = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    w = W.euler_2d_quadrant(n, 2)
+    h = 1.0 / n
+    o = oracle.Mesh(2, 1, 2, win, win, box=(x0 * h, (x0 + win) * h, y0 * h, (y0 + win) * h), bc=W.BC_OUTFLOW)
+    u = o.project_ic(w.ic, w.params[0])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u, _, _ = o.step(u, dt)
+    return win * win * 24 * steps, time.perf_counter() - t0
+
+
+def cpu_oracle_rate(n, dt, win=48, steps=8, workers=None, pool=None):
+    """Oracle DOF-updates/s on the host cores: one spawn-started process per core, each on
+    its own win x win window of the workload (windows straddle the discontinuities)."""
+    import multiprocessing as mp
+    workers = workers or (pool._processes if pool is not None else (os.cpu_count() or 1))
+    rng = np.random.default_rng(0)
+    jobs = []
+    for i in range(workers):
+        y0 = int(np.clip(n // 2 - win // 2 + rng.integers(-win, win), 0, n - win))
+        x0 = int(np.clip(n // 2 - win // 2 + rng.integers(-win, win), 0, n - win))
+        jobs.append(("quadrant", n, y0, x0, win, steps, dt))
+    t0 = time.perf_counter()
+    if pool is None:
+        with mp.get_context("spawn").Pool(workers) as p:
+            res = p.map(_oracle_sample, jobs)
+    else:
+        res = pool.map(_oracle_sample, jobs)
+    wall = time.perf_counter() - t0
+    dof = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return dof / busy, workers, "%d windows of %dx%d cells x %d steps (%.1f s wall)" % (workers, win, win, steps, wall)
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reference_arm(args):
+    """The oracle on the host cores, same metric, bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.size
+    w = W.euler_2d_quadrant(n, 2)
+    # the same fixed time step the GPU arm uses (CFL 0.1 at the initial state's speeds)
+    import oracle
+    rho = [w.params[0][4 * q] for q in range(4)]
+    speeds = []
+    for q in range(4):
+        r, u, v, p = w.params[0][4 * q: 4 * q + 4]
+        c = math.sqrt(1.4 * p / r)
+        speeds.append((abs(u) + c, abs(v) + c))
+    ax, ay = max(s[0] for s in speeds), max(s[1] for s in speeds)
+    dt = 0.1 / (ax * n + ay * n)
+    del rho, oracle
+    import multiprocessing as mp
+    vals = []
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        for i in range(args.warmup + args.steps):
+            rate, cores, sample = cpu_oracle_rate(n, dt, win=32, steps=2, pool=pool)
+            if i >= args.warmup:
+                vals.append(rate)
+    value = float(np.mean(vals))
+    T = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "cells": n * n, "dofs": n * n * 24, "indicator": "tvb",
+                       "limiter": "cswenolimit", "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": T}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-out", default=None)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    # the CPU-baseline pool is started (spawn) before the first GPU call
+    dist, rank, world = dist_init()
+    import torch
+    import paper_1904_11147_gb300 as dgl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n = args.size
+    w = W.euler_2d_quadrant(n, 2)
+    st = torch.cuda.Stream()
+    mesh = dgl.Mesh(2, W.PDE_EULER, 2, [n], [n], w.box, bc=w.bc, stream=st.cuda_stream)
+    mesh.project_ic(w.ic, w.params[0])
+    ws = mesh.max_wavespeed()[0]
+    dt = 0.1 / (ws[0] * n + ws[1] * n)
+    dofs = mesh.size
+    u0 = torch.empty(dofs, dtype=torch.float64, device="cuda")
+    mesh.get_modes(u0)
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(st):
+        # ------------------------------------------------------------ device-resident value
+        for _ in range(args.warmup):
+            mesh.step(dt)
+        st.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        l0 = mesh.launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(args.clocks_out) as clk:
+            e0.record(st)
+            for _ in range(args.steps):
+                mesh.step(dt)
+            e1.record(st)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = mesh.launches - l0
+        barrier(dist)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(dist, ms)
+        value = dofs * args.steps * world / (ms / 1e3)
+        # flagged fraction at the end of the timed region
+        fl = mesh.flag_cells(dgl.IND_TVB, 0.01, want=True)
+        flagged = fl[1] / (n * n)
+
+        # ------------------------------------------------------------ dominant kernel alone
+        mesh.set_modes(u0)
+        mesh.step(dt)
+        st.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        kst = []
+        for _ in range(max(3, min(args.steps, 10))):
+            for s in (1, 2, 3):
+                ev[0].record(st)
+                mesh.rk_stage(s, dt)
+                ev[1].record(st)
+                ev[1].synchronize()
+                kst.append(ev[0].elapsed_time(ev[1]))
+        stage_ms = float(np.mean(kst))
+
+        # ------------------------------------------------------------ end to end (host buffers)
+        host_in = torch.empty(dofs, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(dofs, dtype=torch.float64, pin_memory=True)
+        host_in.copy_(u0.cpu())
+        for _ in range(2):
+            mesh.set_modes(host_in)
+            mesh.step(dt)
+            mesh.get_modes(host_out)
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(st)
+        k_e2e = max(3, args.steps // 2)
+        for _ in range(k_e2e):
+            mesh.set_modes(host_in)
+            mesh.step(dt)
+            mesh.get_modes(host_out)
+        e3.record(st)
+        e3.synchronize()
+        e2e_ms = max(e2.elapsed_time(e3), (time.perf_counter() - t0) * 1e3)
+        e2e_ms = max_over_ranks(dist, e2e_ms)
+    e2e_value = dofs * k_e2e * world / (e2e_ms / 1e3)
+
+    if rank != 0:
+        return 0
+    peaks, src = measured_peaks()
+    fp64_peak = float(peaks.get("fp64_tflops", FP64_NOMINAL_TFLOPS))
+    peak_note = "FP64 nominal 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2.07 GHz); microbenchmark on this pool: 1.20"
+    flops_cell = stage_flops_per_cell(2, 1, 2)
+    achieved = flops_cell * n * n / (stage_ms / 1e3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tr = json.load(open(tpath))
+            if tr.get("kernel_hash") == kernel_hash():
+                traffic = tr["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    cpu_line = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(n, dt, win=48, steps=6)
+        cpu_line = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt, "indicator": "tvb", "tvb_M": 0.01,
+                   "limiter": "cswenolimit", "graph": True, "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
+                   "flagged_fraction_end": flagged, "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": "k_stage2<Euler,P2>", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
+                     "flops_per_cell": flops_cell, "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},
+        "hbm_fraction": dofs * 64 / (ms / args.steps / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+        "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
+        "cpu_baseline": cpu_line,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("dg_kernels2d.cu", "dg_common.cuh", "dg_shared.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1904_11147_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

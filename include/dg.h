@@ -1,0 +1,150 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) RKDG + CSWENO library.
+ *
+ * The library advances u_t + f(u)_x (+ g(u)_y) = 0 (Sec. 2, Eq. (1); Eqs. (19)-(21), (23)
+ * for Burgers and the ideal-gas Euler equations) with a modal discontinuous Galerkin
+ * method, u_h = sum_n U_n psi_n (Eq. (2)), psi_n the orthonormalised Legendre polynomials
+ * on the reference cell (Sec. 2), third-order SSP Runge-Kutta in time (Sec. 3, last
+ * paragraph) and the compact subcell WENO limiter of Sec. 3 on troubled cells.
+ *
+ * Conventions
+ *  - All functions return a dg_status; none aborts or throws.  dg_last_error() gives a
+ *    thread-local description of the last failure.
+ *  - Every call is asynchronous on the mesh's CUDA stream unless it returns host data;
+ *    those synchronise the stream before returning.
+ *  - Modal arrays crossing the ABI use the layout [instance][cell][var][mode] with
+ *    cell = iy * nx + ix, instances concatenated in creation order.  1D: mode n = degree n.
+ *    2D (total degree P^N, (N+1)(N+2)/2 modes): modes are ordered by total degree
+ *    d = a + b, then by b ascending: (0,0),(1,0),(0,1),(2,0),(1,1),(0,2),(3,0),... where
+ *    mode (a,b) is psi_a(r) psi_b(s).  Variables: Burgers u; 1D Euler (rho, rho u, E);
+ *    2D Euler (rho, rho u, rho v, E).
+ *  - Pointers passed in are borrowed for the duration of the call only; the library
+ *    copies what it keeps.  Device memory belongs to the mesh and is freed by
+ *    dg_mesh_destroy.
+ *  - The device layout (SoA planes, tiles) is private.
+ */
+#ifndef DG_H_
+#define DG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mesh dg_mesh; /* opaque, owned by the library */
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = 1,      /* bad argument (sizes, enums, null pointers, order) */
+  DG_ENOMEM = 2,      /* device or host allocation failed */
+  DG_ECUDA = 3,       /* a CUDA runtime call failed (text in dg_last_error) */
+  DG_EPOSITIVITY = 4, /* density or pressure not positive after the fallback */
+  DG_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  DG_ESTATE = 6       /* calls out of order (e.g. stage 2 before stage 1) */
+} dg_status;
+
+typedef enum { DG_BURGERS = 0, DG_EULER = 1 } dg_pde;
+typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 } dg_bc;
+typedef enum { DG_IND_TVB = 0, DG_IND_MLP = 1 } dg_indicator;
+
+/* Initial-condition families for dg_project_ic (parameters per instance):
+ *   DG_IC_SINE          u = p0 + p1 sin(p2 x + p3 y)                              (4)
+ *   DG_IC_RIEMANN1D     (rho,u,p) = p0..p2 for x < p6, p3..p5 otherwise           (7)
+ *   DG_IC_QUADRANT      (rho,u,v,p) for x>=p16,y>=p17: p0..3; x<p16,y>=p17: p4..7;
+ *                       x<p16,y<p17: p8..11; x>=p16,y<p17: p12..15                 (18)
+ *   DG_IC_DENSITY_WAVE  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6     (7) */
+typedef enum { DG_IC_SINE = 0, DG_IC_RIEMANN1D = 1, DG_IC_QUADRANT = 2, DG_IC_DENSITY_WAVE = 3 } dg_ic;
+
+/* Create a batch of n_inst meshes sharing dim, PDE, order N and boundary condition.
+ *  dim      1 or 2.  pde: dg_pde.  N: polynomial degree 1..3 (Sec. 2, P^N).
+ *  nx, ny   host arrays of n_inst cell counts (ny ignored in 1D); each >= 1 (periodic
+ *           meshes need >= 1 cell; the stencil wraps).
+ *  box      host array n_inst * 4: xL, xR, yL, yR of each instance (yL, yR ignored in 1D).
+ *  bc       dg_bc; outflow uses mirror ghost cells (our reading of the paper's
+ *           transmissive shock-tube boundaries, Examples 7-8).
+ *  gamma    ratio of specific heats for Euler (1.4 in the paper), ignored for Burgers.
+ *  stream   a cudaStream_t (may be NULL = legacy default stream).
+ * Allocates three state copies (u^n and two stage buffers) plus flag/list/limiter
+ * scratch on the current device.  Errors: DG_EINVAL, DG_ENOMEM, DG_ECUDA. */
+dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const int* nx, const int* ny,
+                         const double* box, int bc, double gamma, void* stream, dg_mesh** out);
+
+/* Free everything the mesh owns.  NULL is accepted. */
+dg_status dg_mesh_destroy(dg_mesh* m);
+
+/* Number of doubles of a full modal array (sum over instances of cells * vars * modes). */
+size_t dg_mesh_size(const dg_mesh* m);
+
+/* Copy modes in (u^n := modes).  modes is a host (is_device = 0) or device pointer of n
+ * doubles in the ABI layout; n must equal dg_mesh_size.  The copy is ordered on the mesh
+ * stream; a host buffer may be reused once the call returns. */
+dg_status dg_set_modes(dg_mesh* m, const double* modes, size_t n, int is_device);
+
+/* Copy the current state out (the output of the last stage / limiter, or u^n).
+ * Synchronises the stream. */
+dg_status dg_get_modes(dg_mesh* m, double* out, size_t n, int is_device);
+
+/* Initial L2 projection (Eq. (2) applied to u0): U_n = sum_q w_q u0(x_q) psi_n(x_q) with
+ * N+4 Gauss points per direction, computed on the device.  params: host array of
+ * n_inst * nparams doubles (see dg_ic).  Sets u^n. */
+dg_status dg_project_ic(dg_mesh* m, int ic, const double* params, int nparams);
+
+/* Per-instance time steps (host array of n_inst doubles) used by dg_rk_stage / dg_step
+ * when they are called with dt <= 0. */
+dg_status dg_set_dt(dg_mesh* m, const double* dt);
+
+/* One SSP-RK3 stage (Sec. 3, last paragraph; Shu's third-order TVD scheme) of the
+ * semi-discrete scheme of Eq. (5) with the local Lax-Friedrichs flux (Sec. 2):
+ *   stage 1: u1 = u^n + dt L(u^n)
+ *   stage 2: u2 = 3/4 u^n + 1/4 (u1 + dt L(u1))
+ *   stage 3: u^{n+1} = 1/3 u^n + 2/3 (u2 + dt L(u2))
+ * L is evaluated on the current state (the previous stage, limited or not).  dt > 0 applies
+ * to every instance; dt <= 0 uses the per-instance values of dg_set_dt.  No limiting.
+ * Errors: DG_EINVAL (stage not 1..3), DG_ESTATE (stage s without stage s-1 before it). */
+dg_status dg_rk_stage(dg_mesh* m, int stage, double dt);
+
+/* Troubled-cell indicator on the current state (Sec. 3, step 1; the method here uses the
+ * TVB modified minmod with constant tvb_M instead of the paper's KXRCF).  Writes the
+ * device flag array and the compacted list of troubled cells used by dg_cswenolimit.
+ * n_flagged, n_near (cells whose deciding comparison lies within 1e-12 relative of the
+ * threshold) and flags_out (host, one byte per cell) are optional; asking for any of them
+ * synchronises the stream.  Errors: DG_EINVAL (unknown indicator or no MLP weights). */
+dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flagged,
+                        int64_t* n_near, uint8_t* flags_out);
+
+/* CSWENO limiter (Sec. 3, Steps 1-6, Fig. 1) on the cells flagged by the last
+ * dg_flag_cells: keeps each troubled cell's average U_0 and rebuilds modes 1..N from WENO
+ * point values reconstructed on the subcells of its immediate neighbours (characteristic
+ * fields for Euler; dimension by dimension in 2D).  Jacobi update: every troubled cell
+ * reads the unlimited neighbours.  Errors: DG_ESTATE if no flags exist for this state. */
+dg_status dg_cswenolimit(dg_mesh* m);
+
+/* One full SSP-RK3 step: three times (stage, indicator, limiter), replayed from a CUDA
+ * graph captured on the first call.  dt as in dg_rk_stage. */
+dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M);
+
+/* Largest characteristic speed over the cell means of each instance: out[2*i] (x) and
+ * out[2*i+1] (y, 0 in 1D), host array.  Used by callers for the CFL condition.
+ * Synchronises the stream. */
+dg_status dg_max_wavespeed(dg_mesh* m, double* out);
+
+/* Number of kernels the library launched since the mesh was created (graph replays count
+ * every kernel node they contain). */
+int64_t dg_kernel_launches(const dg_mesh* m);
+
+/* Copies the CSWENO tables the library derived for degree N (host only; works without a
+ * GPU).  NG = 2 for N = 1, else 4.  rp[NG], rw[NG]: Step 1 points and weights (Sec. 3);
+ * C[(i*NG+g)*(N+1)+k]: p_i(x_g) from the averages of stencil cells i..i+N (Step 2);
+ * gam[g*(N+1)+i]: Eq. (8); B[(i*(N+1)+k)*(N+1)+l]: Eq. (13) as a quadratic form;
+ * SA[k*(N+1)+n]: average of psi_n over stencil cell k (Fig. 1).  Errors: DG_EINVAL. */
+dg_status dg_limiter_tables(int N, double* rp, double* rw, double* C, double* gam, double* B, double* SA);
+
+/* Thread-local text of the last error (never NULL). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H_ */

@@ -1,0 +1,194 @@
+"""GB300-native RKDG + compact subcell WENO (CSWENO) limiter.
+
+Python binding of the C ABI in ``include/dg.h`` (ctypes; argument marshalling only --
+every step of the method runs in the CUDA kernels of ``libcswenodg.so``).  There is no
+CPU fallback: if the library cannot be loaded, importing ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcswenodg.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EPOSITIVITY, DG_ETIMEOUT, DG_ESTATE = range(7)
+BURGERS, EULER = 0, 1
+BC_PERIODIC, BC_OUTFLOW = 0, 1
+IND_TVB, IND_MLP = 0, 1
+IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EPOSITIVITY",
+                5: "DG_ETIMEOUT", 6: "DG_ESTATE"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _b
+                _b.build()
+            l = ctypes.CDLL(LIB_PATH)
+            D, I, P = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p
+            l.dg_mesh_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, I, I, D,
+                                         ctypes.c_int, ctypes.c_double, P, ctypes.POINTER(P)]
+            l.dg_mesh_destroy.argtypes = [P]
+            l.dg_mesh_size.argtypes = [P]
+            l.dg_mesh_size.restype = ctypes.c_size_t
+            l.dg_set_modes.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int]
+            l.dg_get_modes.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int]
+            l.dg_project_ic.argtypes = [P, ctypes.c_int, D, ctypes.c_int]
+            l.dg_set_dt.argtypes = [P, D]
+            l.dg_rk_stage.argtypes = [P, ctypes.c_int, ctypes.c_double]
+            l.dg_flag_cells.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint8)]
+            l.dg_cswenolimit.argtypes = [P]
+            l.dg_step.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_double]
+            l.dg_max_wavespeed.argtypes = [P, D]
+            l.dg_kernel_launches.argtypes = [P]
+            l.dg_kernel_launches.restype = ctypes.c_int64
+            l.dg_last_error.restype = ctypes.c_char_p
+            l.dg_limiter_tables.argtypes = [ctypes.c_int, D, D, D, D, D, D]
+            for name in ("dg_mesh_create", "dg_mesh_destroy", "dg_set_modes", "dg_get_modes", "dg_project_ic",
+                         "dg_set_dt", "dg_rk_stage", "dg_flag_cells", "dg_cswenolimit", "dg_step",
+                         "dg_max_wavespeed", "dg_limiter_tables"):
+                getattr(l, name).restype = ctypes.c_int
+            _lib = l
+    return _lib
+
+
+def _check(status):
+    if status != DG_OK:
+        raise DGError(status, lib().dg_last_error().decode(errors="replace"))
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def limiter_tables(N: int):
+    """The CSWENO tables the library derived for degree N (host-only call)."""
+    ng = 2 if N == 1 else 4
+    n1 = N + 1
+    rp, rw = np.zeros(ng), np.zeros(ng)
+    C = np.zeros((n1, ng, n1))
+    gam = np.zeros((ng, n1))
+    B = np.zeros((n1, n1, n1))
+    SA = np.zeros((2 * N + 1, n1))
+    _check(lib().dg_limiter_tables(N, _dp(rp), _dp(rw), _dp(C), _dp(gam), _dp(B), _dp(SA)))
+    return dict(pt=rp, wt=rw, C=C, gam=gam, B=B, SA=SA)
+
+
+class Mesh:
+    """A batch of meshes on the current CUDA device (see ``dg_mesh_create``).
+
+    ``stream`` is a raw ``cudaStream_t`` value (e.g. ``torch.cuda.current_stream().cuda_stream``)
+    or 0 for the legacy default stream.
+    """
+
+    def __init__(self, dim, pde, N, nx, ny=None, box=None, bc=BC_PERIODIC, gamma=1.4, stream=0):
+        nx = [int(v) for v in np.atleast_1d(nx)]
+        n_inst = len(nx)
+        ny = [1] * n_inst if (ny is None or dim == 1) else [int(v) for v in np.atleast_1d(ny)]
+        if box is None:
+            box = [(0.0, 1.0, 0.0, 1.0)] * n_inst
+        box = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(n_inst, 4))
+        self.dim, self.pde, self.N, self.n_inst, self.bc = dim, pde, N, n_inst, bc
+        self.nx, self.ny, self.box = nx, ny, box
+        self.nv = 1 if pde == BURGERS else (3 if dim == 1 else 4)
+        self.np = N + 1 if dim == 1 else (N + 1) * (N + 2) // 2
+        self.cells = sum(a * b for a, b in zip(nx, ny))
+        self._h = ctypes.c_void_p()
+        nxa = (ctypes.c_int * n_inst)(*nx)
+        nya = (ctypes.c_int * n_inst)(*ny)
+        _check(lib().dg_mesh_create(dim, pde, N, n_inst, nxa, nya, _dp(box), bc, gamma,
+                                    ctypes.c_void_p(int(stream)), ctypes.byref(self._h)))
+        self.size = int(lib().dg_mesh_size(self._h))
+
+    def close(self):
+        if self._h:
+            lib().dg_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- data movement --------------------------------------------------------------------
+    def set_modes(self, modes):
+        """modes: numpy array (host) or a CUDA tensor (device), layout [cell][var][mode]."""
+        if hasattr(modes, "is_cuda") and modes.is_cuda:
+            assert modes.is_contiguous() and modes.numel() == self.size and str(modes.dtype) == "torch.float64"
+            _check(lib().dg_set_modes(self._h, ctypes.c_void_p(modes.data_ptr()), self.size, 1))
+            return
+        if hasattr(modes, "numpy"):
+            assert str(modes.dtype) == "torch.float64" and modes.is_contiguous() and modes.numel() == self.size
+            _check(lib().dg_set_modes(self._h, ctypes.c_void_p(modes.data_ptr()), self.size, 0))
+            return
+        a = np.ascontiguousarray(modes, dtype=np.float64)
+        assert a.size == self.size
+        _check(lib().dg_set_modes(self._h, a.ctypes.data_as(ctypes.c_void_p), self.size, 0))
+
+    def get_modes(self, out=None):
+        """Returns a numpy array [cell][var][mode], or fills ``out`` (numpy or CUDA tensor)."""
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(lib().dg_get_modes(self._h, ctypes.c_void_p(out.data_ptr()), self.size, 1))
+            return out
+        if out is not None and hasattr(out, "numpy"):
+            _check(lib().dg_get_modes(self._h, ctypes.c_void_p(out.data_ptr()), self.size, 0))
+            return out
+        a = np.empty((self.cells, self.nv, self.np)) if out is None else out
+        _check(lib().dg_get_modes(self._h, a.ctypes.data_as(ctypes.c_void_p), self.size, 0))
+        return a
+
+    def project_ic(self, ic, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(self.n_inst, -1))
+        _check(lib().dg_project_ic(self._h, ic, _dp(p), p.shape[1]))
+
+    def set_dt(self, dt):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n_inst,)))
+        _check(lib().dg_set_dt(self._h, _dp(d)))
+
+    # -- the method ----------------------------------------------------------------------
+    def rk_stage(self, stage, dt):
+        _check(lib().dg_rk_stage(self._h, stage, dt))
+
+    def flag_cells(self, indicator=IND_TVB, M=0.01, want=False):
+        if not want:
+            _check(lib().dg_flag_cells(self._h, indicator, M, None, None, None))
+            return None
+        nf, nn = ctypes.c_int64(0), ctypes.c_int64(0)
+        fl = np.zeros(self.cells, dtype=np.uint8)
+        _check(lib().dg_flag_cells(self._h, indicator, M, ctypes.byref(nf), ctypes.byref(nn),
+                                   fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+        return fl, int(nf.value), int(nn.value)
+
+    def cswenolimit(self):
+        _check(lib().dg_cswenolimit(self._h))
+
+    def step(self, dt, indicator=IND_TVB, M=0.01):
+        _check(lib().dg_step(self._h, dt, indicator, M))
+
+    def max_wavespeed(self):
+        out = np.zeros(2 * self.n_inst)
+        _check(lib().dg_max_wavespeed(self._h, _dp(out)))
+        return out.reshape(self.n_inst, 2)
+
+    @property
+    def launches(self):
+        return int(lib().dg_kernel_launches(self._h))

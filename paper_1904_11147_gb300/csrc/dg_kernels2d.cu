@@ -1,0 +1,917 @@
+// 2D kernels (Cartesian cells, total-degree P^N, N = 1..3; Burgers V = 1, Euler V = 4).
+//
+//   k_stage2    one SSP-RK3 stage of Eq. (5): volume quadrature, traces, local
+//               Lax-Friedrichs fluxes on shared faces, lifting, stage combination
+//   k_flag2     TVB minmod indicator + ballot/scan compaction of troubled cells
+//   k_limit2    CSWENO limiter (Sec. 3), one thread per troubled cell
+//   k_project2  initial L2 projection (Eq. (2))
+//   k_speed2    largest characteristic speed over the cell means
+//
+// FP64 arithmetic is the bound on GB300 (the FP64 pipe runs at 1/64 of FP32), so the
+// kernels are laid out to keep every lane of every FP64 warp instruction useful and to
+// avoid recomputing traces or face fluxes.
+#include "dg_shared.cuh"
+#include "tables.h"
+
+namespace dg {
+namespace k2 {
+
+constexpr int TX = 32;  // tile width = one warp
+constexpr int TY = 8;   // interior rows per tile
+constexpr int kStageThreads = (TY + 3) * 32;
+
+// ----------------------------------------------------------------------------- tables
+template <int N>
+struct Lay {
+  static constexpr int Q = N + 1, NP = (N + 1) * (N + 2) / 2, NS = 2 * N + 1, NG = (N == 1 ? 2 : 4);
+  static constexpr int N1 = N + 1;
+  static constexpr int SIZE_DG = 3 * Q * Q * NP + N1 + 2 * Q * N1;
+  static constexpr int SIZE_FLAG = 4 * NP + 1;
+  static constexpr int SIZE_LIM = NS * N1 + N1 * NG * N1 + NG * N1 + N1 * N1 * N1 + NG * N1 + NG +
+                                  2 * NG * N1 + 3 * NG;
+  static constexpr int SIZE_PROJ = 3 * 8 + 8 * N1;
+  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ;
+};
+__host__ __device__ constexpr int base_of(int N) {
+  return N == 1 ? 0 : (N == 2 ? Lay<1>::SIZE : Lay<1>::SIZE + Lay<2>::SIZE);
+}
+template <int N>
+struct Off {
+  using L = Lay<N>;
+  static constexpr int Q = L::Q, NP = L::NP, NS = L::NS, NG = L::NG, N1 = L::N1;
+  static constexpr int VP = base_of(N);          // [Q*Q][NP] psi_a(x_qx) psi_b(x_qy)
+  static constexpr int VDX = VP + Q * Q * NP;    // w w psi_a'(x_qx) psi_b(x_qy)
+  static constexpr int VDY = VDX + Q * Q * NP;   // w w psi_a(x_qx) psi_b'(x_qy)
+  static constexpr int P1 = VDY + Q * Q * NP;    // psi_n(1)
+  static constexpr int PQ = P1 + N1;             // [Q][N1] psi_n(x_q)
+  static constexpr int WPQ = PQ + Q * N1;        // [Q][N1] w_q psi_n(x_q)
+  static constexpr int TE = WPQ + Q * N1;        // [NP] psi_a(1) psi_b(0)
+  static constexpr int TW = TE + NP;             // psi_a(-1) psi_b(0)
+  static constexpr int TN = TW + NP;             // psi_a(0) psi_b(1)
+  static constexpr int TS = TN + NP;             // psi_a(0) psi_b(-1)
+  static constexpr int C00 = TS + NP;            // psi_0(0)^2
+  static constexpr int SA = C00 + 1;             // [NS][N1]
+  static constexpr int WC = SA + NS * N1;        // [N1 stencil][NG][N1]
+  static constexpr int GAM = WC + N1 * NG * N1;  // [NG][N1]
+  static constexpr int BB = GAM + NG * N1;       // [N1][N1][N1]
+  static constexpr int PG = BB + N1 * N1 * N1;   // [NG][N1] psi_n(r_g)
+  static constexpr int WG = PG + NG * N1;        // [NG]
+  static constexpr int GPN = WG + NG;            // [NG][N1]
+  static constexpr int GMN = GPN + NG * N1;      // [NG][N1]
+  static constexpr int SGP = GMN + NG * N1;      // [NG]
+  static constexpr int SGM = SGP + NG;           // [NG]
+  static constexpr int NEG = SGM + NG;           // [NG] 1.0 where a weight is negative
+  static constexpr int PX = NEG + NG;            // [8]
+  static constexpr int PW = PX + 8;              // [8]
+  static constexpr int PQP = PW + 8;             // [8] (count in slot 0)
+  static constexpr int PP = PQP + 8;             // [8][N1]
+  static constexpr int END = PP + 8 * N1;
+};
+static_assert(Off<3>::END == Lay<1>::SIZE + Lay<2>::SIZE + Lay<3>::SIZE, "table layout");
+constexpr int kTabSize = Off<3>::END;
+
+__constant__ double c_tab[kTabSize];
+
+#define T(x) c_tab[(x)]
+
+template <int N>
+void pack(const dgt::Tabs& t, double* h) {
+  using O = Off<N>;
+  constexpr int Q = O::Q, NP = O::NP, NS = O::NS, NG = O::NG, N1 = O::N1;
+  for (int qy = 0; qy < Q; ++qy)
+    for (int qx = 0; qx < Q; ++qx)
+      for (int m = 0; m < NP; ++m) {
+        int a = mode_a(m), b = mode_b(m), q = qy * Q + qx;
+        double ww = t.gw[qx] * t.gw[qy];
+        h[O::VP + q * NP + m] = t.psi_q[qx][a] * t.psi_q[qy][b];
+        h[O::VDX + q * NP + m] = ww * t.dpsi_q[qx][a] * t.psi_q[qy][b];
+        h[O::VDY + q * NP + m] = ww * t.psi_q[qx][a] * t.dpsi_q[qy][b];
+      }
+  for (int n = 0; n < N1; ++n) h[O::P1 + n] = t.psi_p1[n];
+  for (int q = 0; q < Q; ++q)
+    for (int n = 0; n < N1; ++n) {
+      h[O::PQ + q * N1 + n] = t.psi_q[q][n];
+      h[O::WPQ + q * N1 + n] = t.gw[q] * t.psi_q[q][n];
+    }
+  for (int m = 0; m < NP; ++m) {
+    int a = mode_a(m), b = mode_b(m);
+    h[O::TE + m] = t.psi_p1[a] * t.psi_0[b];
+    h[O::TW + m] = t.psi_m1[a] * t.psi_0[b];
+    h[O::TN + m] = t.psi_0[a] * t.psi_p1[b];
+    h[O::TS + m] = t.psi_0[a] * t.psi_m1[b];
+  }
+  h[O::C00] = t.psi_0[0] * t.psi_0[0];
+  for (int k = 0; k < NS; ++k)
+    for (int n = 0; n < N1; ++n) h[O::SA + k * N1 + n] = t.SA[k][n];
+  for (int i = 0; i < N1; ++i)
+    for (int g = 0; g < NG; ++g)
+      for (int k = 0; k < N1; ++k) h[O::WC + (i * NG + g) * N1 + k] = t.C[i][g][k];
+  for (int g = 0; g < NG; ++g)
+    for (int i = 0; i < N1; ++i) {
+      h[O::GAM + g * N1 + i] = t.gam[g][i];
+      h[O::GPN + g * N1 + i] = t.gpn[g][i];
+      h[O::GMN + g * N1 + i] = t.gmn[g][i];
+    }
+  for (int i = 0; i < N1; ++i)
+    for (int k = 0; k < N1; ++k)
+      for (int l = 0; l < N1; ++l) h[O::BB + (i * N1 + k) * N1 + l] = t.B[i][k][l];
+  for (int g = 0; g < NG; ++g) {
+    for (int n = 0; n < N1; ++n) h[O::PG + g * N1 + n] = t.psiG[g][n];
+    h[O::WG + g] = t.rw[g];
+    h[O::SGP + g] = t.sgp[g];
+    h[O::SGM + g] = t.sgm[g];
+    h[O::NEG + g] = t.neg[g] ? 1.0 : 0.0;
+  }
+  for (int q = 0; q < t.QP; ++q) {
+    h[O::PX + q] = t.px[q];
+    h[O::PW + q] = t.pw[q];
+    for (int n = 0; n < N1; ++n) h[O::PP + q * N1 + n] = t.ppsi[q][n];
+  }
+  h[O::PQP] = t.QP;
+}
+
+// ----------------------------------------------------------------------------- loads
+// Loads the modes of cell (ix, iy) of instance I, applying the boundary condition for
+// ghost cells: periodic wraps; outflow mirrors the boundary cell (modes odd in the
+// normal direction change sign).
+template <int V, int NP>
+__device__ __forceinline__ void load_cell(const double* __restrict__ U, long long ctot, const Inst& I, int ix,
+                                          int iy, int bc, double (&u)[V][NP]) {
+  bool fx = false, fy = false;
+  if (bc == 0) {
+    ix = ix < 0 ? ix + I.nx : (ix >= I.nx ? ix - I.nx : ix);
+    iy = iy < 0 ? iy + I.ny : (iy >= I.ny ? iy - I.ny : iy);
+  } else {
+    if (ix < 0) { ix = 0; fx = true; }
+    if (ix >= I.nx) { ix = I.nx - 1; fx = true; }
+    if (iy < 0) { iy = 0; fy = true; }
+    if (iy >= I.ny) { iy = I.ny - 1; fy = true; }
+  }
+  const long long g = I.off + (long long)iy * I.nx + ix;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      double x = __ldg(U + (long long)(v * NP + m) * ctot + g);
+      bool flip = (fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1));
+      u[v][m] = flip ? -x : x;
+    }
+}
+
+// Traces on the east (r = +1) and west (r = -1) faces at the Q face points:
+// u(+-1, s_q) = sum_b psi_b(s_q) sum_a (+-1)^a U_ab psi_a(1).
+template <int N, int V, int NP>
+__device__ __forceinline__ void traces_x(const double (&u)[V][NP], double (&tE)[N + 1][V], double (&tW)[N + 1][V]) {
+  using O = Off<N>;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double ev[N + 1], od[N + 1];
+#pragma unroll
+    for (int b = 0; b <= N; ++b) {
+      ev[b] = 0.0;
+      od[b] = 0.0;
+#pragma unroll
+      for (int a = 0; a <= N - b; ++a) {
+        double c = u[v][mode_idx(a, b)] * T(O::P1 + a);
+        if (a & 1) od[b] += c; else ev[b] += c;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q <= N; ++q) {
+      double e = 0.0, w = 0.0;
+#pragma unroll
+      for (int b = 0; b <= N; ++b) {
+        e = fma(ev[b] + od[b], T(O::PQ + q * (N + 1) + b), e);
+        w = fma(ev[b] - od[b], T(O::PQ + q * (N + 1) + b), w);
+      }
+      tE[q][v] = e;
+      tW[q][v] = w;
+    }
+  }
+}
+
+// Traces on the north (s = +1) and south (s = -1) faces.
+template <int N, int V, int NP>
+__device__ __forceinline__ void traces_y(const double (&u)[V][NP], double (&tN)[N + 1][V], double (&tS)[N + 1][V]) {
+  using O = Off<N>;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double ev[N + 1], od[N + 1];
+#pragma unroll
+    for (int a = 0; a <= N; ++a) {
+      ev[a] = 0.0;
+      od[a] = 0.0;
+#pragma unroll
+      for (int b = 0; b <= N - a; ++b) {
+        double c = u[v][mode_idx(a, b)] * T(O::P1 + b);
+        if (b & 1) od[a] += c; else ev[a] += c;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q <= N; ++q) {
+      double n = 0.0, s = 0.0;
+#pragma unroll
+      for (int a = 0; a <= N; ++a) {
+        n = fma(ev[a] + od[a], T(O::PQ + q * (N + 1) + a), n);
+        s = fma(ev[a] - od[a], T(O::PQ + q * (N + 1) + a), s);
+      }
+      tN[q][v] = n;
+      tS[q][v] = s;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- stage
+// One tile of TX x TY cells per block.  Warps 0..TY-1 hold the interior rows, warp TY the
+// row below the tile, warp TY+1 the row above it, warp TY+2 the west (lanes 0..15) and
+// east (lanes 16..31) halo cells, so that every trace and every face flux is computed
+// exactly once per tile by a full warp.
+template <int PDE, int N>
+__global__ void __launch_bounds__(kStageThreads, 1)
+    k_stage2(const double* __restrict__ un, const double* __restrict__ us, double* __restrict__ out,
+             const Inst* __restrict__ insts, const Tile* __restrict__ tiles, long long ctot, int bc, int stage,
+             double dt_all, double gam) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1, QV = Q * V;
+  // east traces, then x-face fluxes: [QV][TY][TX+1]; north traces, then y-face fluxes:
+  // [QV][TY+1][TX] (dynamic shared memory, above the 48 KB static limit for Euler P2/P3)
+  extern __shared__ double smem[];
+  double* const sEb = smem;
+  double* const sNb = smem + QV * TY * (TX + 1);
+#define sE(qv, r, c) sEb[((qv) * TY + (r)) * (TX + 1) + (c)]
+#define sN(qv, r, c) sNb[((qv) * (TY + 1) + (r)) * TX + (c)]
+  const Tile tile = tiles[blockIdx.x];
+  const Inst I = insts[tile.inst];
+  const int ncols = min(TX, I.nx - tile.x0), nrows = min(TY, I.ny - tile.y0);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double gm1 = gam - 1.0;
+  const double sx = 2.0 / I.hx, sy = 2.0 / I.hy, ihx = 1.0 / I.hx, ihy = 1.0 / I.hy;
+
+  const bool interior = w < TY && w < nrows && lane < ncols;
+  double acc[V][NP];
+  double trW[Q][V], trS[Q][V];
+  // ---------------------------------------------------------------- phase 1
+  if (interior) {
+    double u[V][NP];
+    load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 + w, bc, u);
+    double tE[Q][V], tN[Q][V];
+    traces_x<N>(u, tE, trW);
+    traces_y<N>(u, tN, trS);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        sE(q * V + v, w, lane + 1) = tE[q][v];
+        sN(q * V + v, w + 1, lane) = tN[q][v];
+      }
+    // volume term: (2/hx) sum_q w w f psi_a' psi_b + (2/hy) sum_q w w g psi_a psi_b'
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc[v][m] = 0.0;
+#pragma unroll
+    for (int qy = 0; qy < Q; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < Q; ++qx) {
+        const int q = qy * Q + qx;
+        double uq[V], f[V], g[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          double s = u[v][0] * T(O::VP + q * NP);
+#pragma unroll
+          for (int m = 1; m < NP; ++m) s = fma(u[v][m], T(O::VP + q * NP + m), s);
+          uq[v] = s;
+        }
+        vol_flux2<2, PDE>(uq, f, g, sx, sy, gm1);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int m = 1; m < NP; ++m) {
+            if (mode_a(m) >= 1) acc[v][m] = fma(f[v], T(O::VDX + q * NP + m), acc[v][m]);
+            if (mode_b(m) >= 1) acc[v][m] = fma(g[v], T(O::VDY + q * NP + m), acc[v][m]);
+          }
+      }
+  } else if (w == TY) {  // row below the tile: its north traces
+    if (lane < ncols) {
+      double u[V][NP], tN[Q][V], tS[Q][V];
+      load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 - 1, bc, u);
+      traces_y<N>(u, tN, tS);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) sN(q * V + v, 0, lane) = tN[q][v];
+    }
+  } else if (w == TY + 1) {  // row above the tile: its south traces (kept for phase 2)
+    if (lane < ncols) {
+      double u[V][NP], tN[Q][V];
+      load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 + nrows, bc, u);
+      traces_y<N>(u, tN, trS);
+    }
+  } else if (w == TY + 2) {  // west halo (lanes < 16) east traces, east halo west traces
+    const bool east = lane >= 16;
+    const int row = east ? lane - 16 : lane;
+    if (row < nrows) {
+      double u[V][NP], tA[Q][V], tB[Q][V];
+      load_cell<V, NP>(us, ctot, I, east ? tile.x0 + ncols : tile.x0 - 1, tile.y0 + row, bc, u);
+      traces_x<N>(u, tA, tB);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          if (!east) sE(q * V + v, row, 0) = tA[q][v];
+          trW[q][v] = tB[q][v];
+        }
+    }
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- phase 2: face fluxes
+  if (interior) {
+    double uL[V], uR[V], fs[V];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        uL[v] = sE(q * V + v, w, lane);
+        uR[v] = trW[q][v];
+      }
+      llf<2, PDE>(0, uL, uR, fs, ihx, gam, gm1);
+#pragma unroll
+      for (int v = 0; v < V; ++v) sE(q * V + v, w, lane) = fs[v];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        uL[v] = sN(q * V + v, w, lane);
+        uR[v] = trS[q][v];
+      }
+      llf<2, PDE>(1, uL, uR, fs, ihy, gam, gm1);
+#pragma unroll
+      for (int v = 0; v < V; ++v) sN(q * V + v, w, lane) = fs[v];
+    }
+  } else if (w == TY + 1) {
+    if (lane < ncols) {
+      double uL[V], fs[V];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) uL[v] = sN(q * V + v, nrows, lane);
+        llf<2, PDE>(1, uL, trS[q], fs, ihy, gam, gm1);
+#pragma unroll
+        for (int v = 0; v < V; ++v) sN(q * V + v, nrows, lane) = fs[v];
+      }
+    }
+  } else if (w == TY + 2) {
+    const int row = lane - 16;
+    if (lane >= 16 && row < nrows) {
+      double uL[V], fs[V];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) uL[v] = sE(q * V + v, row, ncols);
+        llf<2, PDE>(0, uL, trW[q], fs, ihx, gam, gm1);
+#pragma unroll
+        for (int v = 0; v < V; ++v) sE(q * V + v, row, ncols) = fs[v];
+      }
+    }
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- phase 3: lift + RK
+  if (!interior) return;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    // x faces: acc_ab -= psi_a(1) sum_q w_q psi_b(s_q) [F_E(q) - (-1)^a F_W(q)]
+    double dxs[Q], sxs[Q], dys[Q], sys[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      double fe = sE(q * V + v, w, lane + 1), fw = sE(q * V + v, w, lane);
+      double fn = sN(q * V + v, w + 1, lane), fsv = sN(q * V + v, w, lane);
+      dxs[q] = fe - fw;
+      sxs[q] = fe + fw;
+      dys[q] = fn - fsv;
+      sys[q] = fn + fsv;
+    }
+#pragma unroll
+    for (int b = 0; b <= N; ++b) {
+      double Sp = 0.0, Sm = 0.0, Tp = 0.0, Tm = 0.0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const double c = T(O::WPQ + q * (N + 1) + b);
+        Sp = fma(c, dxs[q], Sp);
+        Sm = fma(c, sxs[q], Sm);
+        Tp = fma(c, dys[q], Tp);
+        Tm = fma(c, sys[q], Tm);
+      }
+      // here b plays the transverse index: x faces use psi_b(s), y faces psi_a(r)
+#pragma unroll
+      for (int a = 0; a <= N - b; ++a) {
+        const int mx = mode_idx(a, b);  // x faces: transverse degree b, normal degree a
+        acc[v][mx] = fma(-T(O::P1 + a), (a & 1) ? Sm : Sp, acc[v][mx]);
+        const int my = mode_idx(b, a);  // y faces: transverse degree b (in x), normal a
+        acc[v][my] = fma(-T(O::P1 + a), (a & 1) ? Tm : Tp, acc[v][my]);
+      }
+    }
+  }
+  const long long g = I.off + (long long)(tile.y0 + w) * I.nx + tile.x0 + lane;
+  const double dt = dt_all > 0.0 ? dt_all : I.dt;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      const long long idx = (long long)(v * NP + m) * ctot + g;
+      double e = fma(dt, acc[v][m], us[idx]);
+      double r;
+      if (stage == 1) r = e;
+      else if (stage == 2) r = fma(0.75, un[idx], 0.25 * e);
+      else r = fma(1.0 / 3.0, un[idx], (2.0 / 3.0) * e);
+      out[idx] = r;
+    }
+}
+
+#undef sE
+#undef sN
+
+// ----------------------------------------------------------------------------- indicator
+// TVB modified minmod (Cockburn-Shu) on conserved variables, x test on the east/west
+// edge midpoints and y test on the north/south ones.  The face values and means are
+// formed without fused multiply-adds and in the same order as a plain serial sum, so the
+// decision is reproducible bit for bit.  near: a deciding comparison within 1e-12 relative.
+__device__ __forceinline__ bool tvb_changes(double a1, double a2, double a3, double Mh2, bool& near) {
+  const double rel = 1e-12;
+  const double b1 = fabs(a1);
+  if (fabs(b1 - Mh2) <= rel * fmax(b1, Mh2)) near = true;
+  if (b1 <= Mh2) return false;
+  const double s = fmax(fmax(b1, fabs(a2)), fabs(a3));
+  if (fabs(a2) <= rel * s || fabs(a3) <= rel * s) near = true;
+  double mt;
+  if (a1 > 0 && a2 > 0 && a3 > 0) mt = fmin(fmin(a1, a2), a3);
+  else if (a1 < 0 && a2 < 0 && a3 < 0) mt = fmax(fmax(a1, a2), a3);
+  else mt = 0.0;
+  if (mt != 0.0) {
+    const double m23 = fmin(fabs(a2), fabs(a3));
+    if (fabs(b1 - m23) <= rel * fmax(b1, m23)) near = true;
+  }
+  return mt != a1;
+}
+
+template <int PDE, int N>
+__global__ void __launch_bounds__(256)
+    k_flag2(const double* __restrict__ U, const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+            long long ctot, int bc, double M, unsigned char* __restrict__ flags, Counters* cnt,
+            int* __restrict__ list_cell, int* __restrict__ list_inst) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N);
+  const Tile tile = tiles[blockIdx.x];
+  const Inst I = insts[tile.inst];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ix = tile.x0 + lane, iy = tile.y0 + w;
+  const bool active = ix < I.nx && iy < I.ny;
+  int fl = 0;
+  bool near = false;
+  long long g = 0;
+  if (active) {
+    g = I.off + (long long)iy * I.nx + ix;
+    // neighbour cells (outflow ghosts have the boundary cell's mean)
+    auto nb = [&](int jx, int jy) -> long long {
+      if (bc == 0) {
+        jx = jx < 0 ? jx + I.nx : (jx >= I.nx ? jx - I.nx : jx);
+        jy = jy < 0 ? jy + I.ny : (jy >= I.ny ? jy - I.ny : jy);
+      } else {
+        jx = jx < 0 ? 0 : (jx >= I.nx ? I.nx - 1 : jx);
+        jy = jy < 0 ? 0 : (jy >= I.ny ? I.ny - 1 : jy);
+      }
+      return I.off + (long long)jy * I.nx + jx;
+    };
+    const long long gW = nb(ix - 1, iy), gE = nb(ix + 1, iy), gS = nb(ix, iy - 1), gN = nb(ix, iy + 1);
+    const double c00 = T(O::C00);
+    const double Mx = M * I.hx * I.hx, My = M * I.hy * I.hy;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const double* P = U + (long long)(v * NP) * ctot;
+      const double mean = __dmul_rn(__ldg(P + g), c00);
+      const double mW = __dmul_rn(__ldg(P + gW), c00), mE = __dmul_rn(__ldg(P + gE), c00);
+      const double mS = __dmul_rn(__ldg(P + gS), c00), mN = __dmul_rn(__ldg(P + gN), c00);
+      double uE = 0.0, uW = 0.0, uN = 0.0, uS = 0.0;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const double ck = __ldg(P + (long long)m * ctot + g);
+        uE = __dadd_rn(uE, __dmul_rn(ck, T(O::TE + m)));
+        uW = __dadd_rn(uW, __dmul_rn(ck, T(O::TW + m)));
+        uN = __dadd_rn(uN, __dmul_rn(ck, T(O::TN + m)));
+        uS = __dadd_rn(uS, __dmul_rn(ck, T(O::TS + m)));
+      }
+      const double dpx = __dsub_rn(mE, mean), dmx = __dsub_rn(mean, mW);
+      const double dpy = __dsub_rn(mN, mean), dmy = __dsub_rn(mean, mS);
+      fl |= tvb_changes(__dsub_rn(uE, mean), dpx, dmx, Mx, near);
+      fl |= tvb_changes(__dsub_rn(mean, uW), dpx, dmx, Mx, near);
+      fl |= tvb_changes(__dsub_rn(uN, mean), dpy, dmy, My, near);
+      fl |= tvb_changes(__dsub_rn(mean, uS), dpy, dmy, My, near);
+    }
+    flags[g] = (unsigned char)fl;
+  }
+  block_compact(fl, near ? 1 : 0, g, tile.inst, cnt, list_cell, list_inst);
+}
+
+// ----------------------------------------------------------------------------- limiter
+// One WENO reconstruction (Sec. 3, Steps 2-5) from the 2N+1 stencil averages to the NG
+// Step 1 points.  Eq. (14) read as wbar_i = gamma_i / (eps + beta_i)^2; where a linear
+// weight is negative (P3) the split gamma = sigma+ gamma~+ - sigma- gamma~- of Shi, Hu and
+// Shu is used, each part normalised separately.
+template <int N>
+__device__ __forceinline__ void weno(const double* avg, double* out) {
+  using O = Off<N>;
+  constexpr int N1 = N + 1, NG = O::NG;
+  const double eps = 1e-6;
+  // beta_i and p_i - c do not change when a constant c is removed from all averages
+  // (constants are reproduced; Eq. (13) holds only derivatives): work on averages
+  // centred at the troubled cell's own, which avoids cancellation in beta.
+  const double c = avg[N];
+  double dv[2 * N + 1];
+#pragma unroll
+  for (int k = 0; k < 2 * N + 1; ++k) dv[k] = avg[k] - c;
+  double inv[N1];
+#pragma unroll
+  for (int i = 0; i < N1; ++i) {
+    double beta = 0.0;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+      double r = 0.0;
+#pragma unroll
+      for (int l = 0; l < N1; ++l) r = fma(T(O::BB + (i * N1 + k) * N1 + l), dv[i + l], r);
+      beta = fma(dv[i + k], r, beta);
+    }
+    const double d = eps + beta;
+    inv[i] = 1.0 / (d * d);
+  }
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    double p[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) s = fma(T(O::WC + (i * NG + g) * N1 + k), dv[i + k], s);
+      p[i] = c + s;
+    }
+    if (T(O::NEG + g) == 0.0) {
+      double sw = 0.0, su = 0.0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const double wb = T(O::GAM + g * N1 + i) * inv[i];
+        sw += wb;
+        su = fma(wb, p[i], su);
+      }
+      out[g] = su / sw;
+    } else {
+      double swp = 0.0, sup = 0.0, swm = 0.0, sum = 0.0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const double wp = T(O::GPN + g * N1 + i) * inv[i];
+        const double wm = T(O::GMN + g * N1 + i) * inv[i];
+        swp += wp;
+        sup = fma(wp, p[i], sup);
+        swm += wm;
+        sum = fma(wm, p[i], sum);
+      }
+      out[g] = T(O::SGP + g) * (sup / swp) - T(O::SGM + g) * (sum / swm);
+    }
+  }
+}
+
+// Right/left eigenvectors of the 2D Euler flux Jacobian in direction dir at state u.
+__device__ __forceinline__ void euler_eig2(const double* u, int dir, double gam, double (&R)[4][4],
+                                           double (&L)[4][4]) {
+  const double rho = u[0], r = 1.0 / rho;
+  const double vx = u[1] * r, vy = u[2] * r, q2 = vx * vx + vy * vy;
+  const double p = (gam - 1.0) * (u[3] - 0.5 * rho * q2);
+  const double c = sqrt(gam * p * r), ic = 1.0 / c;
+  const double H = (u[3] + p) * r;
+  const double b1 = (gam - 1.0) * ic * ic, b2 = 0.5 * b1 * q2;
+  const double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
+  const int in = dir == 0 ? 1 : 2, it = dir == 0 ? 2 : 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { R[i][j] = 0.0; L[i][j] = 0.0; }
+  R[0][0] = 1.0; R[in][0] = vn - c; R[it][0] = vt; R[3][0] = H - vn * c;
+  R[0][1] = 1.0; R[in][1] = vn;     R[it][1] = vt; R[3][1] = 0.5 * q2;
+  R[it][2] = 1.0; R[3][2] = vt;
+  R[0][3] = 1.0; R[in][3] = vn + c; R[it][3] = vt; R[3][3] = H + vn * c;
+  L[0][0] = 0.5 * (b2 + vn * ic); L[0][in] = -0.5 * (b1 * vn + ic); L[0][it] = -0.5 * b1 * vt; L[0][3] = 0.5 * b1;
+  L[1][0] = 1.0 - b2;             L[1][in] = b1 * vn;               L[1][it] = b1 * vt;        L[1][3] = -b1;
+  L[2][0] = -vt;                  L[2][it] = 1.0;
+  L[3][0] = 0.5 * (b2 - vn * ic); L[3][in] = 0.5 * (ic - b1 * vn);  L[3][it] = -0.5 * b1 * vt; L[3][3] = 0.5 * b1;
+}
+
+// CSWENO on the listed cells; thread i handles list entry i.  Output: the limited modes
+// 1..NP-1 in list order (lim[(v*NP + m) * cap + i]).
+template <int PDE, int N>
+__global__ void __launch_bounds__(128)
+    k_limit2(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc,
+             const int* __restrict__ list_cell, const int* __restrict__ list_inst, const Counters* __restrict__ cnt,
+             double* __restrict__ lim, long long cap, double gam) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N), NS = O::NS, NG = O::NG, N1 = N + 1;
+  const unsigned int n = cnt->n_flag;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long g = list_cell[i];
+    const Inst I = insts[list_inst[i]];
+    const int loc = (int)(g - I.off);
+    const int ix = loc % I.nx, iy = loc / I.nx;
+    // (2N+1)^2 sub-rectangle averages of the 3x3 neighbourhood (Fig. 1 in each direction)
+    double avg[V][NS][NS];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        double u[V][NP];
+        load_cell<V, NP>(U, ctot, I, ix + dx, iy + dy, bc, u);
+        constexpr int k0[3] = {0, N, N + 1};
+        constexpr int kn[3] = {N, 1, N};
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int kx = k0[dx + 1]; kx < k0[dx + 1] + kn[dx + 1]; ++kx) {
+            double t[N1];  // t_b = sum_a U_ab SA[kx][a]
+#pragma unroll
+            for (int b = 0; b <= N; ++b) {
+              double s = 0.0;
+#pragma unroll
+              for (int a = 0; a <= N - b; ++a) s = fma(u[v][mode_idx(a, b)], T(O::SA + kx * N1 + a), s);
+              t[b] = s;
+            }
+#pragma unroll
+            for (int ky = k0[dy + 1]; ky < k0[dy + 1] + kn[dy + 1]; ++ky) {
+              double s = 0.0;
+#pragma unroll
+              for (int b = 0; b <= N; ++b) s = fma(t[b], T(O::SA + ky * N1 + b), s);
+              avg[v][ky][kx] = s;
+            }
+          }
+      }
+    // x sweep: rowval[v][ky][g] = average over row ky of u(x_g, y)
+    double rowv[V][NS][NG];
+    double pv[V][NG][NG];  // [v][gy][gx]
+    if constexpr (PDE == 1) {
+      double mean[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) mean[v] = __ldg(U + (long long)(v * NP) * ctot + g) * T(O::C00);
+      double R[4][4], L[4][4];
+      euler_eig2(mean, 0, gam, R, L);
+#pragma unroll
+      for (int ky = 0; ky < NS; ++ky) {
+        double wv[4][NG];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          double wc[NS];
+#pragma unroll
+          for (int kx = 0; kx < NS; ++kx) {
+            double s = 0.0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              s = fma(L[f][v], avg[v][ky][kx], s);
+            wc[kx] = s;
+          }
+          weno<N>(wc, wv[f]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int q = 0; q < NG; ++q) {
+            double s = 0.0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s = fma(R[v][f], wv[f][q], s);
+            rowv[v][ky][q] = s;
+          }
+      }
+      euler_eig2(mean, 1, gam, R, L);
+#pragma unroll
+      for (int gx = 0; gx < NG; ++gx) {
+        double wv[4][NG];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          double wc[NS];
+#pragma unroll
+          for (int ky = 0; ky < NS; ++ky) {
+            double s = 0.0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) s = fma(L[f][v], rowv[v][ky][gx], s);
+            wc[ky] = s;
+          }
+          weno<N>(wc, wv[f]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int gy = 0; gy < NG; ++gy) {
+            double s = 0.0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) s = fma(R[v][f], wv[f][gy], s);
+            pv[v][gy][gx] = s;
+          }
+      }
+    } else {
+#pragma unroll
+      for (int ky = 0; ky < NS; ++ky) weno<N>(avg[0][ky], rowv[0][ky]);
+#pragma unroll
+      for (int gx = 0; gx < NG; ++gx) {
+        double col[NS], r[NG];
+#pragma unroll
+        for (int ky = 0; ky < NS; ++ky) col[ky] = rowv[0][ky][gx];
+        weno<N>(col, r);
+#pragma unroll
+        for (int gy = 0; gy < NG; ++gy) pv[0][gy][gx] = r[gy];
+      }
+    }
+    // Step 6 (Eq. (16)) with the tensor rule: U_ab = sum w_gx w_gy u psi_a(x_gx) psi_b(y_gy)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      double tq[NG][N1];  // tq[gy][a] = sum_gx w_gx psi_a(x_gx) pv[gy][gx]
+#pragma unroll
+      for (int gy = 0; gy < NG; ++gy)
+#pragma unroll
+        for (int a = 0; a <= N; ++a) {
+          double s = 0.0;
+#pragma unroll
+          for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WG + gx) * T(O::PG + gx * N1 + a), pv[v][gy][gx], s);
+          tq[gy][a] = s;
+        }
+#pragma unroll
+      for (int m = 1; m < NP; ++m) {
+        const int a = mode_a(m), b = mode_b(m);
+        double s = 0.0;
+#pragma unroll
+        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WG + gy) * T(O::PG + gy * N1 + b), tq[gy][a], s);
+        lim[(long long)(v * NP + m) * cap + i] = s;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- projection
+// Eq. (2) for the initial data: U_ab = sum_{qx,qy} w w u0(x, y) psi_a psi_b with N+4 Gauss
+// points per direction.  Parameters per instance (see dg.h for the families).
+__device__ __forceinline__ void ic_eval2(int kind, const double* p, double x, double y, double gam, int pde,
+                                         double* u) {
+  if (kind == 0) { u[0] = p[0] + p[1] * sin(p[2] * x + p[3] * y); return; }
+  double rho, vx, vy, pr;
+  if (kind == 2) {
+    const int q = (x >= p[16]) ? (y >= p[17] ? 0 : 3) : (y >= p[17] ? 1 : 2);
+    rho = p[4 * q]; vx = p[4 * q + 1]; vy = p[4 * q + 2]; pr = p[4 * q + 3];
+  } else {  // density wave
+    rho = p[0] + p[1] * sin(p[2] * x + p[3] * y); vx = p[4]; vy = p[5]; pr = p[6];
+  }
+  u[0] = rho; u[1] = rho * vx; u[2] = rho * vy; u[3] = pr / (gam - 1.0) + 0.5 * rho * (vx * vx + vy * vy);
+  (void)pde;
+}
+
+template <int PDE, int N>
+__global__ void k_project2(double* __restrict__ U, const Inst* __restrict__ insts, const int* __restrict__ cell_inst,
+                           long long ncell, long long ctot, int kind, const double* __restrict__ params, int np,
+                           double gam) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N), N1 = N + 1;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ncell) return;
+  const int ii = cell_inst[g];
+  const Inst I = insts[ii];
+  const int loc = (int)(g - I.off), ix = loc % I.nx, iy = loc / I.nx;
+  const double* p = params + (long long)ii * np;
+  const int QP = (int)T(O::PQP);
+  double acc[V][NP];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) acc[v][m] = 0.0;
+  for (int qy = 0; qy < QP; ++qy)
+    for (int qx = 0; qx < QP; ++qx) {
+      const double x = I.xL + I.hx * (ix + 0.5 * (1.0 + T(O::PX + qx)));
+      const double y = I.yL + I.hy * (iy + 0.5 * (1.0 + T(O::PX + qy)));
+      double u[V];
+      ic_eval2(kind, p, x, y, gam, PDE, u);
+      const double ww = T(O::PW + qx) * T(O::PW + qy);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const double c = ww * T(O::PP + qx * N1 + mode_a(m)) * T(O::PP + qy * N1 + mode_b(m));
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v][m] = fma(c, u[v], acc[v][m]);
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) U[(long long)(v * NP + m) * ctot + g] = acc[v][m];
+}
+
+template <int PDE, int N>
+__global__ void k_speed2(const double* __restrict__ U, const Inst* __restrict__ insts, const int* __restrict__ cell_inst,
+                         long long ncell, long long ctot, double gam, double* out) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N);
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= ncell) return;
+  double u[V];
+  for (int v = 0; v < V; ++v) u[v] = U[(long long)(v * NP) * ctot + g] * T(O::C00);
+  double sx, sy;
+  if constexpr (PDE == 0) {
+    sx = sy = fabs(u[0]);
+  } else {
+    const double r = 1.0 / u[0], vx = u[1] * r, vy = u[2] * r;
+    const double p = (gam - 1.0) * (u[3] - 0.5 * u[0] * (vx * vx + vy * vy));
+    const double c = sqrt(gam * p * r);
+    sx = fabs(vx) + c;
+    sy = fabs(vy) + c;
+  }
+  const int ii = cell_inst[g];
+  atomic_max_nonneg(out + 2 * ii, sx);
+  atomic_max_nonneg(out + 2 * ii + 1, sy);
+}
+
+#undef T
+
+}  // namespace k2
+
+// ----------------------------------------------------------------------------- host side
+
+cudaError_t upload_tables2(const dgt::Tabs* tabs /* [3] for N = 1..3 */) {
+  static double h[k2::kTabSize];
+  for (int i = 0; i < k2::kTabSize; ++i) h[i] = 0.0;
+  k2::pack<1>(tabs[0], h);
+  k2::pack<2>(tabs[1], h);
+  k2::pack<3>(tabs[2], h);
+  return cudaMemcpyToSymbol(k2::c_tab, h, sizeof(h));
+}
+
+#define DG_DISPATCH2(PDE, N, CALL) \
+  do {                                                   \
+    if ((PDE) == 0 && (N) == 1) { constexpr int P_ = 0, N_ = 1; CALL; } \
+    else if ((PDE) == 0 && (N) == 2) { constexpr int P_ = 0, N_ = 2; CALL; } \
+    else if ((PDE) == 0 && (N) == 3) { constexpr int P_ = 0, N_ = 3; CALL; } \
+    else if ((PDE) == 1 && (N) == 1) { constexpr int P_ = 1, N_ = 1; CALL; } \
+    else if ((PDE) == 1 && (N) == 2) { constexpr int P_ = 1, N_ = 2; CALL; } \
+    else { constexpr int P_ = 1, N_ = 3; CALL; } \
+  } while (0)
+
+int stage_threads2() { return k2::kStageThreads; }
+
+template <int PDE, int N>
+static size_t stage_smem2() {
+  constexpr int QV = (N + 1) * nv_of(2, PDE);
+  return sizeof(double) * (size_t)(QV * k2::TY * (k2::TX + 1) + QV * (k2::TY + 1) * k2::TX);
+}
+
+template <int PDE, int N>
+static cudaError_t prep_stage2() {
+  // opt in to more than 48 KB of dynamic shared memory (set per device, outside captures)
+  return cudaFuncSetAttribute(k2::k_stage2<PDE, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)stage_smem2<PDE, N>());
+}
+
+cudaError_t prepare2(int pde, int N) {
+  cudaError_t e = cudaSuccess;
+  DG_DISPATCH2(pde, N, (e = prep_stage2<P_, N_>()));
+  return e;
+}
+
+template <int PDE, int N>
+static void run_stage2(const LaunchArgs& a, int stage, double dt_all) {
+  const size_t bytes = stage_smem2<PDE, N>();
+  k2::k_stage2<PDE, N><<<a.ntiles, k2::kStageThreads, bytes, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
+                                                                       a.bc, stage, dt_all, a.gam);
+}
+int tile_w2() { return k2::TX; }
+int tile_h2() { return k2::TY; }
+
+void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all) {
+  DG_DISPATCH2(pde, N, (run_stage2<P_, N_>(a, stage, dt_all)));
+}
+
+void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc,
+                  int* li) {
+  DG_DISPATCH2(pde, N, (k2::k_flag2<P_, N_><<<a.ntiles, 256, 0, a.st>>>(a.us, a.inst, a.tiles, a.ctot, a.bc, M,
+                                                                          flags, cnt, lc, li)));
+}
+
+void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
+                   double* lim, int nblocks) {
+  DG_DISPATCH2(pde, N, (k2::k_limit2<P_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt,
+                                                                          lim, a.cap, a.gam)));
+}
+
+void launch_scatter2(int pde, int N, const LaunchArgs& a, const double* lim, const int* lc, const Counters* cnt,
+                     int nblocks) {
+  DG_DISPATCH2(pde, N, (k_scatter<nv_of(2, P_), np_of(2, N_)><<<nblocks, 256, 0, a.st>>>(
+                           a.out, a.ctot, lim, a.cap, lc, cnt)));
+}
+
+void launch_project2(int pde, int N, const LaunchArgs& a, const int* cell_inst, int kind, const double* params,
+                     int np) {
+  const int nb = (int)((a.ncell + 127) / 128);
+  DG_DISPATCH2(pde, N, (k2::k_project2<P_, N_><<<nb, 128, 0, a.st>>>(a.out, a.inst, cell_inst, a.ncell, a.ctot,
+                                                                       kind, params, np, a.gam)));
+}
+
+void launch_speed2(int pde, int N, const LaunchArgs& a, const int* cell_inst, double* out) {
+  const int nb = (int)((a.ncell + 255) / 256);
+  DG_DISPATCH2(pde, N, (k2::k_speed2<P_, N_><<<nb, 256, 0, a.st>>>(a.us, a.inst, cell_inst, a.ncell, a.ctot,
+                                                                     a.gam, out)));
+}
+
+}  // namespace dg

@@ -1,0 +1,84 @@
+// Device helpers shared by the 1D and 2D kernel files: block compaction of flagged
+// cells, the scatter of limited modes, and an atomic max on non-negative doubles.
+#pragma once
+
+#include "dg_common.cuh"
+
+namespace dg {
+
+// Arguments shared by the launchers of one kernel family (1D or 2D).
+struct LaunchArgs {
+  cudaStream_t st;
+  const double *un, *us;
+  double* out;
+  const Inst* inst;
+  const Tile* tiles;
+  int ntiles;
+  long long ctot, ncell, cap;
+  int bc;
+  double gam;
+};
+
+// Per-call device counters (one struct per mesh, zeroed before each indicator pass).
+struct Counters {
+  unsigned int n_flag;   // number of troubled cells in the list
+  unsigned int n_near;   // cells decided within 1e-12 relative of a threshold
+  unsigned int status;   // device error bits
+  unsigned int pad;
+};
+
+// Compacts the calling block's flagged cells into list[] with one atomic per block.
+// Every thread of the block must call it (flag = 0 for inactive threads).
+// Warp ballot + shared-memory scan of the warp totals (up to 32 warps per block).
+__device__ __forceinline__ void block_compact(int flag, int near, long long cell, int inst,
+                                              Counters* cnt, int* list_cell, int* list_inst) {
+  __shared__ unsigned int s_warp[32];
+  __shared__ unsigned int s_base;
+  __shared__ unsigned int s_near;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) s_near = 0;
+  unsigned int bal = __ballot_sync(0xffffffffu, flag);
+  unsigned int nbal = __ballot_sync(0xffffffffu, near);
+  if (lane == 0) s_warp[w] = __popc(bal);
+  __syncthreads();
+  if (lane == 0 && nbal) atomicAdd(&s_near, (unsigned)__popc(nbal));
+  if (threadIdx.x == 0) {
+    unsigned int run = 0;
+    for (int i = 0; i < nw; ++i) {
+      unsigned int c = s_warp[i];
+      s_warp[i] = run;
+      run += c;
+    }
+    s_base = run ? atomicAdd(&cnt->n_flag, run) : 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_near) atomicAdd(&cnt->n_near, s_near);
+  if (flag) {
+    unsigned int pos = s_base + s_warp[w] + __popc(bal & ((1u << lane) - 1u));
+    list_cell[pos] = (int)cell;
+    list_inst[pos] = inst;
+  }
+}
+
+// Writes the limited modes 1..NP-1 of every listed cell back into the state planes.
+// lim is [(v*NP + m) * cap + i] (compact, list order).
+template <int V, int NP>
+__global__ void k_scatter(double* __restrict__ U, long long ctot, const double* __restrict__ lim, long long cap,
+                          const int* __restrict__ list_cell, const Counters* __restrict__ cnt) {
+  const unsigned int n = cnt->n_flag;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    long long g = list_cell[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int m = 1; m < NP; ++m) U[(long long)(v * NP + m) * ctot + g] = lim[(long long)(v * NP + m) * cap + i];
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns as signed 64-bit integers
+  atomicMax(reinterpret_cast<long long*>(addr), __double_as_longlong(v));
+}
+
+}  // namespace dg
