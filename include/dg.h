@@ -141,6 +141,35 @@ int64_t dg_kernel_launches(const dg_mesh* m);
  * SA[k*(N+1)+n]: average of psi_n over stencil cell k (Fig. 1).  Errors: DG_EINVAL. */
 dg_status dg_limiter_tables(int N, double* rp, double* rw, double* C, double* gam, double* B, double* SA);
 
+/* Largest mesh (cells) that dg_cswenolimit_noalloc accepts. */
+#define DG_NOALLOC_MAX_CELLS 16384
+
+/* The troubled-cell indicator (TVB, as dg_flag_cells) and the CSWENO limiter (as
+ * dg_cswenolimit) for one mesh in one call that allocates no device memory.  The paper has
+ * no counterpart: this entry point exists for callers that must not allocate once they run
+ * -- an application whose memory manager already reserved or capped the GPU memory, a
+ * latency-critical loop in which cudaMalloc/cudaFree could block on or synchronise with
+ * the device, or a plugin whose host forbids allocation after initialisation.
+ *  dim, pde, N, bc, gamma, tvb_M  as for dg_mesh_create / dg_flag_cells; one instance of
+ *           nx x ny cells (ny ignored in 1D) on box = {xL, xR, yL, yR} (host array).
+ *  u_in     device array, V*NP planes of nx*ny doubles: plane (v*NP + m) holds mode m of
+ *           variable v for cell iy*nx + ix (modes and variables ordered as in the ABI layout).
+ *  u_out    device array of the same shape; may equal u_in (limited in place).  Unflagged
+ *           cells are copied; flagged cells keep U_0 and get limited modes 1..N.
+ *  n_flagged  optional host pointer; if given, the call synchronises the stream and stores
+ *           the number of troubled cells.
+ *  stream   cudaStream_t (NULL = legacy default stream); the work is ordered on it.
+ * Scratch: a file-scope device array of about 5.7 MB (sized for DG_NOALLOC_MAX_CELLS cells of
+ * up to 4 variables x 10 modes), created when the library's device code is loaded and kept
+ * until the process exits on every GPU that loads the library.  The first call on a device
+ * uploads the method's tables and looks the array up with that device current; make that
+ * first call before any stream capture.  Every call uses the same array and the array keeps
+ * the last call's contents (the call clears the counters it needs at zero), so calls that
+ * overlap on the GPU (other streams, other host threads) race: order them.
+ * Errors: DG_EINVAL (bad arguments, or more than DG_NOALLOC_MAX_CELLS cells), DG_ECUDA. */
+dg_status dg_cswenolimit_noalloc(int dim, int pde, int N, int nx, int ny, const double* box, int bc, double gamma,
+                                 double tvb_M, const double* u_in, double* u_out, int64_t* n_flagged, void* stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char* dg_last_error(void);
 

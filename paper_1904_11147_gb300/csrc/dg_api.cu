@@ -59,11 +59,13 @@ static dg_status fail(dg_status s, const char* fmt, ...) {
 
 extern "C" const char* dg_last_error(void) { return g_err; }
 
+void dg_set_error_internal(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 // ----------------------------------------------------------------------------- tables
 static int g_tables_dev = -2;  // device the constant tables were uploaded to (per process)
 static dgt::Tabs g_tabs[3];
 
-static dg_status ensure_tables() {
+dg_status dg_ensure_tables_internal() {
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (g_tables_dev == -2) {
@@ -146,7 +148,7 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (n_inst < 1 || !nx || !box || (dim == 2 && !ny)) return fail(DG_EINVAL, "bad instance arrays");
   if (bc != DG_BC_PERIODIC && bc != DG_BC_OUTFLOW) return fail(DG_EINVAL, "unknown bc %d", bc);
   if (pde == DG_EULER && !(gamma > 1.0)) return fail(DG_EINVAL, "gamma must exceed 1");
-  dg_status s = ensure_tables();
+  dg_status s = dg_ensure_tables_internal();
   if (s != DG_OK) return s;
   dg_mesh* m = new (std::nothrow) dg_mesh();
   if (!m) return fail(DG_ENOMEM, "host allocation");
