@@ -47,7 +47,8 @@ def stage_flops_per_cell(dim: int, pde: int, N: int) -> int:
     ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
     n_dx = sum(1 for a, b in ab if a >= 1)
     n_dy = sum(1 for a, b in ab if b >= 1)
-    evalf = Q * Q * V * (2 * NP - 1)
+    # sum-factorised evaluation: t_b(x) for every x point, then u at every (x, y) point
+    evalf = Q * V * (N + 1) ** 2 + Q * Q * V * (2 * (N + 1) - 1)
     flux = Q * Q * (24 if pde == 1 else 4)
     proj = Q * Q * V * 2 * (n_dx + n_dy)
     traces = 2 * V * (2 * NP + 2 * (N + 1) + Q * (N + 1) * 4)

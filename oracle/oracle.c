@@ -21,6 +21,7 @@
  * outflow boundaries, dimension-by-dimension (x then y) 2D reconstruction.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -592,18 +593,28 @@ void or_rk_stage(const or_mesh* m, int stage, double dt, const double* un, const
  *   mt(a1,a2,a3) = a1 if |a1| <= M h^2, else minmod(a1,a2,a3).
  * Conserved variables; in 2D the x test uses the east/west edge midpoints and the y test
  * the north/south ones, with h the cell width in that direction.  A cell is also counted
- * "near threshold" when one of the comparisons deciding it is within 1e-12 relative.
+ * "near threshold" when one of the comparisons deciding it is within about 1e-12 relative
+ * (see ulp_near).
  * ----------------------------------------------------------------------------------*/
+/* Near-threshold window (reporting only): two non-negative doubles are "near" when their
+ * IEEE-754 bit patterns differ by at most 8192 units in the last place (a relative
+ * difference between 0.9e-12 and 1.8e-12); a mean difference is "near zero" when it is
+ * at most 2^-40 (about 0.9e-12) of the largest magnitude in the comparison. */
+static int ulp_near(double x, double y) {
+  int64_t a, b;
+  memcpy(&a, &x, sizeof a);
+  memcpy(&b, &y, sizeof b);
+  return a - b <= 8192 && a - b >= -8192;
+}
+
 static int tvb_changes(double a1, double a2, double a3, double Mh2, int* near) {
-  const double rel = 1e-12;
   double b1 = fabs(a1);
-  double mx = b1 > Mh2 ? b1 : Mh2;
-  if (fabs(b1 - Mh2) <= rel * mx) *near = 1;
+  if (ulp_near(b1, Mh2)) *near = 1;
   double mt;
   if (b1 <= Mh2) return 0;
   double s = fabs(a1) > fabs(a2) ? fabs(a1) : fabs(a2);
   s = s > fabs(a3) ? s : fabs(a3);
-  if (fabs(a2) <= rel * s || fabs(a3) <= rel * s) *near = 1;
+  if (fabs(a2) <= ldexp(s, -40) || fabs(a3) <= ldexp(s, -40)) *near = 1;
   if (a1 > 0 && a2 > 0 && a3 > 0) {
     mt = a1 < a2 ? a1 : a2;
     mt = mt < a3 ? mt : a3;
@@ -615,8 +626,7 @@ static int tvb_changes(double a1, double a2, double a3, double Mh2, int* near) {
   }
   if (mt != 0.0) {
     double m23 = fabs(a2) < fabs(a3) ? fabs(a2) : fabs(a3);
-    double mm = b1 > m23 ? b1 : m23;
-    if (fabs(b1 - m23) <= rel * mm) *near = 1;
+    if (ulp_near(b1, m23)) *near = 1;
   }
   return mt != a1;
 }

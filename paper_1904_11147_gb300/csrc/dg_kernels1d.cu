@@ -185,24 +185,6 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
-__device__ __forceinline__ bool tvb_changes(double a1, double a2, double a3, double Mh2, bool& near) {
-  const double rel = 1e-12;
-  const double b1 = fabs(a1);
-  if (fabs(b1 - Mh2) <= rel * fmax(b1, Mh2)) near = true;
-  if (b1 <= Mh2) return false;
-  const double s = fmax(fmax(b1, fabs(a2)), fabs(a3));
-  if (fabs(a2) <= rel * s || fabs(a3) <= rel * s) near = true;
-  double mt;
-  if (a1 > 0 && a2 > 0 && a3 > 0) mt = fmin(fmin(a1, a2), a3);
-  else if (a1 < 0 && a2 < 0 && a3 < 0) mt = fmax(fmax(a1, a2), a3);
-  else mt = 0.0;
-  if (mt != 0.0) {
-    const double m23 = fmin(fabs(a2), fabs(a3));
-    if (fabs(b1 - m23) <= rel * fmax(b1, m23)) near = true;
-  }
-  return mt != a1;
-}
-
 // TVB minmod flags (see the 2D kernel); mean = U_0 psi_0, face values by a plain
 // serial sum without fused multiply-adds.
 template <int PDE, int N>
@@ -228,7 +210,7 @@ __global__ void __launch_bounds__(kBlock)
       jl = jl < 0 ? 0 : jl;
       jr = jr >= I.nx ? I.nx - 1 : jr;
     }
-    const double Mh2 = M * I.hx * I.hx;
+    const long long mh2 = __double_as_longlong(M * I.hx * I.hx);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const double* P = U + (long long)(v * N1) * ctot;
@@ -237,14 +219,14 @@ __global__ void __launch_bounds__(kBlock)
       const double mL = __dmul_rn(__ldg(P + I.off + jl), p0), mR = __dmul_rn(__ldg(P + I.off + jr), p0);
       double up = 0.0, um = 0.0;
 #pragma unroll
-      for (int n = 0; n < N1; ++n) {
-        const double c = __ldg(P + (long long)n * ctot + g);
-        up = __dadd_rn(up, __dmul_rn(c, T(O::P1 + n)));
-        um = __dadd_rn(um, __dmul_rn(c, T(O::M1 + n)));
+      for (int n = 0; n < N1; ++n) {  // psi_n(-1) = (-1)^n psi_n(1): one product per mode
+        const double pc = __dmul_rn(__ldg(P + (long long)n * ctot + g), T(O::P1 + n));
+        up = __dadd_rn(up, pc);
+        um = (n & 1) ? __dsub_rn(um, pc) : __dadd_rn(um, pc);
       }
       const double dp = __dsub_rn(mR, mean), dm = __dsub_rn(mean, mL);
-      fl |= tvb_changes(__dsub_rn(up, mean), dp, dm, Mh2, near);
-      fl |= tvb_changes(__dsub_rn(mean, um), dp, dm, Mh2, near);
+      fl |= tvb_changes_bits(__dsub_rn(up, mean), dp, dm, mh2, near);
+      fl |= tvb_changes_bits(__dsub_rn(mean, um), dp, dm, mh2, near);
     }
     flags[g] = (unsigned char)fl;
   }

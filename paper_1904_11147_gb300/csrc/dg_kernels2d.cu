@@ -221,6 +221,35 @@ __device__ __forceinline__ void traces_y(const double (&u)[V][NP], double (&tN)[
   }
 }
 
+// Trace on one face at the Q face points for halo cells, which need a single side:
+// dir 0: east face (r = +1); dir 1: north face (s = +1).  A halo cell that needs the west
+// (south) trace passes its modes with the odd normal degrees negated (mirror image).
+template <int N, int V, int NP>
+__device__ __forceinline__ void trace_one(const double (&u)[V][NP], int dir, double (&tr)[N + 1][V]) {
+  using O = Off<N>;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double e[N + 1];
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {  // t: transverse degree
+      double s = 0.0;
+#pragma unroll
+      for (int n = 0; n <= N - t; ++n) {  // n: normal degree
+        const int m = dir == 0 ? mode_idx(n, t) : mode_idx(t, n);
+        s = fma(u[v][m], T(O::P1 + n), s);
+      }
+      e[t] = s;
+    }
+#pragma unroll
+    for (int q = 0; q <= N; ++q) {
+      double r = 0.0;
+#pragma unroll
+      for (int t = 0; t <= N; ++t) r = fma(e[t], T(O::PQ + q * (N + 1) + t), r);
+      tr[q][v] = r;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- stage
 // One tile of TX x TY cells per block.  Warps 0..TY-1 hold the interior rows, warp TY the
 // row below the tile, warp TY+1 the row above it, warp TY+2 the west (lanes 0..15) and
@@ -270,17 +299,28 @@ __global__ void __launch_bounds__(kStageThreads, 1)
 #pragma unroll
       for (int m = 0; m < NP; ++m) acc[v][m] = 0.0;
 #pragma unroll
-    for (int qy = 0; qy < Q; ++qy)
+    for (int qx = 0; qx < Q; ++qx) {
+      // sum factorisation: t_b(x_qx) = sum_a U_ab psi_a(x_qx), then u = sum_b t_b psi_b(y_qy)
+      double tb[V][N + 1];
 #pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int b = 0; b <= N; ++b) {
+          double t = u[v][mode_idx(0, b)] * T(O::PQ + qx * (N + 1));
+#pragma unroll
+          for (int a = 1; a <= N - b; ++a) t = fma(u[v][mode_idx(a, b)], T(O::PQ + qx * (N + 1) + a), t);
+          tb[v][b] = t;
+        }
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) {
         const int q = qy * Q + qx;
         double uq[V], f[V], g[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          double s = u[v][0] * T(O::VP + q * NP);
+          double t = tb[v][0] * T(O::PQ + qy * (N + 1));
 #pragma unroll
-          for (int m = 1; m < NP; ++m) s = fma(u[v][m], T(O::VP + q * NP + m), s);
-          uq[v] = s;
+          for (int b = 1; b <= N; ++b) t = fma(tb[v][b], T(O::PQ + qy * (N + 1) + b), t);
+          uq[v] = t;
         }
         vol_flux2<2, PDE>(uq, f, g, sx, sy, gm1);
 #pragma unroll
@@ -291,11 +331,12 @@ __global__ void __launch_bounds__(kStageThreads, 1)
             if (mode_b(m) >= 1) acc[v][m] = fma(g[v], T(O::VDY + q * NP + m), acc[v][m]);
           }
       }
+    }
   } else if (w == TY) {  // row below the tile: its north traces
     if (lane < ncols) {
-      double u[V][NP], tN[Q][V], tS[Q][V];
+      double u[V][NP], tN[Q][V];
       load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 - 1, bc, u);
-      traces_y<N>(u, tN, tS);
+      trace_one<N>(u, 1, tN);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -303,23 +344,33 @@ __global__ void __launch_bounds__(kStageThreads, 1)
     }
   } else if (w == TY + 1) {  // row above the tile: its south traces (kept for phase 2)
     if (lane < ncols) {
-      double u[V][NP], tN[Q][V];
+      double u[V][NP];
       load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 + nrows, bc, u);
-      traces_y<N>(u, tN, trS);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+          if (mode_b(m) & 1) u[v][m] = -u[v][m];
+      trace_one<N>(u, 1, trS);
     }
   } else if (w == TY + 2) {  // west halo (lanes < 16) east traces, east halo west traces
     const bool east = lane >= 16;
     const int row = east ? lane - 16 : lane;
     if (row < nrows) {
-      double u[V][NP], tA[Q][V], tB[Q][V];
+      double u[V][NP], tA[Q][V];
       load_cell<V, NP>(us, ctot, I, east ? tile.x0 + ncols : tile.x0 - 1, tile.y0 + row, bc, u);
-      traces_x<N>(u, tA, tB);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+          if (east && (mode_a(m) & 1)) u[v][m] = -u[v][m];
+      trace_one<N>(u, 0, tA);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           if (!east) sE(q * V + v, row, 0) = tA[q][v];
-          trW[q][v] = tB[q][v];
+          trW[q][v] = tA[q][v];
         }
     }
   }
@@ -431,25 +482,9 @@ __global__ void __launch_bounds__(kStageThreads, 1)
 // ----------------------------------------------------------------------------- indicator
 // TVB modified minmod (Cockburn-Shu) on conserved variables, x test on the east/west
 // edge midpoints and y test on the north/south ones.  The face values and means are
-// formed without fused multiply-adds and in the same order as a plain serial sum, so the
-// decision is reproducible bit for bit.  near: a deciding comparison within 1e-12 relative.
-__device__ __forceinline__ bool tvb_changes(double a1, double a2, double a3, double Mh2, bool& near) {
-  const double rel = 1e-12;
-  const double b1 = fabs(a1);
-  if (fabs(b1 - Mh2) <= rel * fmax(b1, Mh2)) near = true;
-  if (b1 <= Mh2) return false;
-  const double s = fmax(fmax(b1, fabs(a2)), fabs(a3));
-  if (fabs(a2) <= rel * s || fabs(a3) <= rel * s) near = true;
-  double mt;
-  if (a1 > 0 && a2 > 0 && a3 > 0) mt = fmin(fmin(a1, a2), a3);
-  else if (a1 < 0 && a2 < 0 && a3 < 0) mt = fmax(fmax(a1, a2), a3);
-  else mt = 0.0;
-  if (mt != 0.0) {
-    const double m23 = fmin(fabs(a2), fabs(a3));
-    if (fabs(b1 - m23) <= rel * fmax(b1, m23)) near = true;
-  }
-  return mt != a1;
-}
+// formed without fused multiply-adds and in the order of a plain serial sum over the
+// modes, so the decision is reproducible bit for bit; products whose table factor is
+// exactly zero (psi_b(0) for odd b) are skipped, which leaves every partial sum unchanged.
 
 template <int PDE, int N>
 __global__ void __launch_bounds__(256)
@@ -481,7 +516,7 @@ __global__ void __launch_bounds__(256)
     };
     const long long gW = nb(ix - 1, iy), gE = nb(ix + 1, iy), gS = nb(ix, iy - 1), gN = nb(ix, iy + 1);
     const double c00 = T(O::C00);
-    const double Mx = M * I.hx * I.hx, My = M * I.hy * I.hy;
+    const long long mx2 = __double_as_longlong(M * I.hx * I.hx), my2 = __double_as_longlong(M * I.hy * I.hy);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const double* P = U + (long long)(v * NP) * ctot;
@@ -491,18 +526,25 @@ __global__ void __launch_bounds__(256)
       double uE = 0.0, uW = 0.0, uN = 0.0, uS = 0.0;
 #pragma unroll
       for (int m = 0; m < NP; ++m) {
+        const int a = mode_a(m), b = mode_b(m);
         const double ck = __ldg(P + (long long)m * ctot + g);
-        uE = __dadd_rn(uE, __dmul_rn(ck, T(O::TE + m)));
-        uW = __dadd_rn(uW, __dmul_rn(ck, T(O::TW + m)));
-        uN = __dadd_rn(uN, __dmul_rn(ck, T(O::TN + m)));
-        uS = __dadd_rn(uS, __dmul_rn(ck, T(O::TS + m)));
+        if (!(b & 1)) {  // psi_b(0) != 0: east/west products (west = (-1)^a east)
+          const double pe = __dmul_rn(ck, T(O::TE + m));
+          uE = __dadd_rn(uE, pe);
+          uW = (a & 1) ? __dsub_rn(uW, pe) : __dadd_rn(uW, pe);
+        }
+        if (!(a & 1)) {  // psi_a(0) != 0: north/south products (south = (-1)^b north)
+          const double pn = __dmul_rn(ck, T(O::TN + m));
+          uN = __dadd_rn(uN, pn);
+          uS = (b & 1) ? __dsub_rn(uS, pn) : __dadd_rn(uS, pn);
+        }
       }
       const double dpx = __dsub_rn(mE, mean), dmx = __dsub_rn(mean, mW);
       const double dpy = __dsub_rn(mN, mean), dmy = __dsub_rn(mean, mS);
-      fl |= tvb_changes(__dsub_rn(uE, mean), dpx, dmx, Mx, near);
-      fl |= tvb_changes(__dsub_rn(mean, uW), dpx, dmx, Mx, near);
-      fl |= tvb_changes(__dsub_rn(uN, mean), dpy, dmy, My, near);
-      fl |= tvb_changes(__dsub_rn(mean, uS), dpy, dmy, My, near);
+      fl |= tvb_changes_bits(__dsub_rn(uE, mean), dpx, dmx, mx2, near);
+      fl |= tvb_changes_bits(__dsub_rn(mean, uW), dpx, dmx, mx2, near);
+      fl |= tvb_changes_bits(__dsub_rn(uN, mean), dpy, dmy, my2, near);
+      fl |= tvb_changes_bits(__dsub_rn(mean, uS), dpy, dmy, my2, near);
     }
     flags[g] = (unsigned char)fl;
   }
