@@ -253,8 +253,24 @@ def main():
     n = args.size
     w = W.euler_2d_quadrant(n, 2)
     st = torch.cuda.Stream()
-    mesh = dgl.Mesh(2, W.PDE_EULER, 2, [n], [n], w.box, bc=w.bc, stream=st.cuda_stream)
-    mesh.project_ic(w.ic, w.params[0])
+
+    # learned indicator: harvested from the plain method on other seeded problems, trained
+    # and calibrated with the library's kernels (untimed)
+    from paper_1904_11147_gb300 import train as T
+    t_train = time.perf_counter()
+    with torch.cuda.stream(st):
+        net, tau, tinfo = T.train_indicator(stream=st)
+    st.synchronize()
+    t_train = time.perf_counter() - t_train
+
+    def make_mesh(learned):
+        m = dgl.Mesh(2, W.PDE_EULER, 2, [n], [n], w.box, bc=w.bc, stream=st.cuda_stream)
+        m.project_ic(w.ic, w.params[0])
+        if learned:
+            m.set_indicator(net, tau)
+        return m
+
+    mesh = make_mesh(False)
     ws = mesh.max_wavespeed()[0]
     dt = 0.1 / (ws[0] * n + ws[1] * n)
     dofs = mesh.size
@@ -262,30 +278,36 @@ def main():
     mesh.get_modes(u0)
     torch.cuda.synchronize()
 
-    with torch.cuda.stream(st):
-        # ------------------------------------------------------------ device-resident value
+    def timed_arm(m, ind, clk_path):
         for _ in range(args.warmup):
-            mesh.step(dt)
+            m.step(dt, ind)
         st.synchronize()
+        m.flag_statistics(reset=True)
         barrier(dist)
         torch.cuda.synchronize()
-        l0 = mesh.launches
+        l0 = m.launches
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(args.clocks_out) as clk:
+        with ClockSampler(clk_path) as clk:
             e0.record(st)
             for _ in range(args.steps):
-                mesh.step(dt)
+                m.step(dt, ind)
             e1.record(st)
             e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        launches = mesh.launches - l0
+        ms_ = e0.elapsed_time(e1)
+        launches_ = m.launches - l0
         barrier(dist)
         torch.cuda.synchronize()
-        ms = max_over_ranks(dist, ms)
+        ms_ = max_over_ranks(dist, ms_)
+        tvbf, limited, passes = m.flag_statistics()
+        return ms_, launches_, clk, tvbf / max(passes, 1) / (n * n), limited / max(passes, 1) / (n * n)
+
+    with torch.cuda.stream(st):
+        ms_plain, _, clk_plain, tvb_frac, lim_plain = timed_arm(mesh, dgl.IND_TVB, None)
+        lmesh = make_mesh(True)
+        ms, launches, clk, _, lim_learned = timed_arm(lmesh, dgl.IND_MLP, args.clocks_out)
+        fallbacks, failures = lmesh.positivity_report()
         value = dofs * args.steps * world / (ms / 1e3)
-        # flagged fraction at the end of the timed region
-        fl = mesh.flag_cells(dgl.IND_TVB, 0.01, want=True)
-        flagged = fl[1] / (n * n)
+        value_plain = dofs * args.steps * world / (ms_plain / 1e3)
 
         # ------------------------------------------------------------ dominant kernel alone
         mesh.set_modes(u0)
@@ -307,9 +329,9 @@ def main():
         host_out = torch.empty(dofs, dtype=torch.float64, pin_memory=True)
         host_in.copy_(u0.cpu())
         for _ in range(2):
-            mesh.set_modes(host_in)
-            mesh.step(dt)
-            mesh.get_modes(host_out)
+            lmesh.set_modes(host_in)
+            lmesh.step(dt, dgl.IND_MLP)
+            lmesh.get_modes(host_out)
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -318,14 +340,15 @@ def main():
         e2.record(st)
         k_e2e = max(3, args.steps // 2)
         for _ in range(k_e2e):
-            mesh.set_modes(host_in)
-            mesh.step(dt)
-            mesh.get_modes(host_out)
+            lmesh.set_modes(host_in)
+            lmesh.step(dt, dgl.IND_MLP)
+            lmesh.get_modes(host_out)
         e3.record(st)
         e3.synchronize()
         e2e_ms = max(e2.elapsed_time(e3), (time.perf_counter() - t0) * 1e3)
         e2e_ms = max_over_ranks(dist, e2e_ms)
     e2e_value = dofs * k_e2e * world / (e2e_ms / 1e3)
+    flagged = lim_learned
 
     if rank != 0:
         return 0
@@ -351,9 +374,17 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt, "indicator": "tvb", "tvb_M": 0.01,
-                   "limiter": "cswenolimit", "graph": True, "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
-                   "flagged_fraction_end": flagged, "parallelism": "replicas" if world > 1 else "single"},
+        "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt, "indicator": "learned (TVB-gated MLP)",
+                   "tvb_M": 0.01, "limiter": "cswenolimit", "graph": True,
+                   "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "learned": {"value": value, "ms_per_step": ms / args.steps, "limited_fraction": lim_learned, "tau": tau,
+                    "positivity_fallbacks": fallbacks, "positivity_failures": failures,
+                    "train_s": t_train, "val_recall": tinfo["val_recall"], "label_tol": tinfo["tol"],
+                    "val_kept_of_tvb": tinfo["val_predicted"] / max(tinfo["val_tvb_flagged"], 1)},
+        "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps, "limited_fraction": lim_plain,
+                  "tvb_flagged_fraction": tvb_frac},
+        "learned_over_plain": value / value_plain,
         "roofline": {"bound": "alu", "kernel": "k_stage2<Euler,P2>", "achieved": achieved, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                      "flops_per_cell": flops_cell, "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},
@@ -363,6 +394,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": dofs * 8, "d2h_bytes_per_step": dofs * 8},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "clocks_plain_arm": clk_plain.summary(),
     }
     print(json.dumps(line))
     if dist is not None:

@@ -141,6 +141,76 @@ int64_t dg_kernel_launches(const dg_mesh* m);
  * SA[k*(N+1)+n]: average of psi_n over stencil cell k (Fig. 1).  Errors: DG_EINVAL. */
 dg_status dg_limiter_tables(int N, double* rp, double* rw, double* C, double* gam, double* B, double* SA);
 
+/* ------------------------------------------------------------------------------------
+ * Learned troubled-cell indicator (the paper has none; its Sec. 3 indicator is KXRCF and
+ * this library's plain indicator is the TVB minmod).  A 32-32 ReLU network maps features
+ * of a cell and its cross neighbours to one logit; a cell is troubled when logit > tau.
+ * Features per variable v (s_v = max_c |ubar_c - ubar_j| + sum_{n>=1} |U^j_{n,v}| + 1e-14):
+ * (ubar_c - ubar_j)/s_v for the neighbours c (W, E, S, N; 1D: L, R), then U^c_{n,v}/s_v for
+ * n >= 1 and c = the cell, then the neighbours in that order.  Inference runs inside the
+ * flagging pass on the tensor cores (BF16 weights and features, FP32 accumulation); the
+ * network is trained on the device by this library's kernels from harvested tuples.
+ * ----------------------------------------------------------------------------------*/
+typedef struct dg_mlp dg_mlp; /* network + Adam state, owned by the library */
+
+/* Number of features for (dim, pde, N): V (4 + 5 (NP-1)) in 2D, V (2 + 3 N) in 1D; -1 if invalid. */
+int dg_mlp_features(int dim, int pde, int N);
+
+/* New network for n_features inputs, He-uniform weights from seed, zero biases and Adam
+ * moments; its kernels run on stream.  Errors: DG_EINVAL, DG_ENOMEM. */
+dg_status dg_mlp_create(int n_features, uint64_t seed, void* stream, dg_mlp** out);
+dg_status dg_mlp_destroy(dg_mlp* n);
+
+/* Parameters as one FP32 host vector: W1 [32][F] (row = hidden unit), b1 [32], W2 [32][32],
+ * b2 [32], w3 [32], b3 [1]; count = 32 F + 1121.  set also resets the Adam moments. */
+size_t dg_mlp_param_count(const dg_mlp* n);
+dg_status dg_mlp_get_params(dg_mlp* n, float* out, size_t count);
+dg_status dg_mlp_set_params(dg_mlp* n, const float* in, size_t count);
+
+/* Gradient (host, packed as the parameters) and mean loss of the weighted binary cross
+ * entropy -[pw y log s(z) + (1-y) log(1-s(z))] over B samples; X: device [B][F] FP32,
+ * y: device [B] bytes (0/1).  FP32 arithmetic.  Synchronises the network's stream. */
+dg_status dg_mlp_grad(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pos_weight, float* grad_out,
+                      float* loss_out);
+
+/* One Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected) on the batch; loss_out (host,
+ * optional) receives the batch loss before the step and synchronises. */
+dg_status dg_mlp_train_step(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pos_weight, float lr,
+                            float* loss_out);
+
+/* FP32 logits of B samples (X device [B][F], logits device [B]), asynchronous on the
+ * network's stream; for validation and for choosing the threshold. */
+dg_status dg_mlp_predict(dg_mlp* n, const float* X, int64_t B, float* logits);
+
+/* Attach the network's current weights to the mesh as DG_IND_MLP with threshold tau.
+ * DG_IND_MLP flags a cell when the TVB indicator flags it and the network's logit exceeds
+ * tau (the network filters the TVB list).  In dg_step, Euler instances whose limited stage
+ * has a non-positive density or pressure at a quadrature point (FP32 screen with a 1e-6 E
+ * margin) are limited again with the plain TVB flags from their unlimited state. */
+dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau);
+
+/* Evaluates the network on every cell of the current state and writes the logits to the
+ * device array logits [cells] (FP32); also sets the flags (logit > tau, without the TVB gate)
+ * that the next dg_cswenolimit uses.  Diagnostics of the learned indicator. */
+dg_status dg_indicator_logits(dg_mesh* m, float* logits);
+
+/* Training data from the plain method on the current (post-stage, unlimited) state:
+ * features X (device [cells][F] FP32), TVB flags (device [cells] bytes) and the limiter's
+ * relative change (device [cells] FP32: for a flagged cell max over v and n >= 1 of
+ * |limited - unlimited U_{n,v}| / s_v, 0 for the others); then applies the TVB + CSWENO
+ * limiter to the state as dg_flag_cells(TVB) + dg_cswenolimit would. */
+dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* change);
+
+/* Running totals over the limiter passes of dg_step (three per step): cells the TVB
+ * indicator flagged, cells actually limited (equal for DG_IND_TVB; the learned subset for
+ * DG_IND_MLP) and the number of passes.  reset != 0 zeroes them.  Synchronises the stream. */
+dg_status dg_flag_statistics(dg_mesh* m, int64_t* tvb_flagged, int64_t* limited, int64_t* passes, int reset);
+
+/* Positivity fallbacks of the learned indicator since the network was attached: instance
+ * stages that fell back to the TVB flags, and those still non-positive after it.  Returns
+ * DG_EPOSITIVITY when failures > 0.  Synchronises the stream. */
+dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures);
+
 /* Largest mesh (cells) that dg_cswenolimit_noalloc accepts. */
 #define DG_NOALLOC_MAX_CELLS 16384
 

@@ -62,9 +62,30 @@ def lib():
             l.dg_kernel_launches.restype = ctypes.c_int64
             l.dg_last_error.restype = ctypes.c_char_p
             l.dg_limiter_tables.argtypes = [ctypes.c_int, D, D, D, D, D, D]
+            F = ctypes.POINTER(ctypes.c_float)
+            l.dg_mlp_features.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            l.dg_mlp_create.argtypes = [ctypes.c_int, ctypes.c_uint64, P, ctypes.POINTER(P)]
+            l.dg_mlp_destroy.argtypes = [P]
+            l.dg_mlp_param_count.argtypes = [P]
+            l.dg_mlp_param_count.restype = ctypes.c_size_t
+            l.dg_mlp_get_params.argtypes = [P, F, ctypes.c_size_t]
+            l.dg_mlp_set_params.argtypes = [P, F, ctypes.c_size_t]
+            l.dg_mlp_grad.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_float, F, F]
+            l.dg_mlp_train_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, F]
+            l.dg_set_indicator_mlp.argtypes = [P, P, ctypes.c_float]
+            l.dg_mlp_predict.argtypes = [P, P, ctypes.c_int64, P]
+            l.dg_positivity_report.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+            l.dg_positivity_report.restype = ctypes.c_int
+            l.dg_flag_statistics.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+            l.dg_flag_statistics.restype = ctypes.c_int
+            l.dg_indicator_logits.argtypes = [P, P]
+            l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             for name in ("dg_mesh_create", "dg_mesh_destroy", "dg_set_modes", "dg_get_modes", "dg_project_ic",
                          "dg_set_dt", "dg_rk_stage", "dg_flag_cells", "dg_cswenolimit", "dg_step",
-                         "dg_max_wavespeed", "dg_limiter_tables"):
+                         "dg_max_wavespeed", "dg_limiter_tables", "dg_mlp_create", "dg_mlp_destroy",
+                         "dg_mlp_get_params", "dg_mlp_set_params", "dg_mlp_grad", "dg_mlp_train_step",
+                         "dg_set_indicator_mlp", "dg_indicator_logits", "dg_harvest", "dg_mlp_predict"):
                 getattr(l, name).restype = ctypes.c_int
             _lib = l
     return _lib
@@ -192,3 +213,81 @@ class Mesh:
     @property
     def launches(self):
         return int(lib().dg_kernel_launches(self._h))
+
+    # -- learned indicator -------------------------------------------------------------
+    def harvest(self, X, flags, change, M=0.01):
+        """Features, TVB flags and the limiter's relative change of the current state into
+        CUDA tensors (float32, uint8, float32), then limits the state with the TVB indicator."""
+        _check(lib().dg_harvest(self._h, M, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(flags.data_ptr()),
+                                ctypes.c_void_p(change.data_ptr())))
+
+    def set_indicator(self, net, tau=0.0):
+        _check(lib().dg_set_indicator_mlp(self._h, net._h, tau))
+
+    def flag_statistics(self, reset=False):
+        """(TVB-flagged, limited, passes) totals over the dg_step limiter passes."""
+        a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().dg_flag_statistics(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
+        return int(a.value), int(b.value), int(c.value)
+
+    def positivity_report(self):
+        """(fallbacks, failures) of the learned indicator's positivity screen."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        lib().dg_positivity_report(self._h, ctypes.byref(a), ctypes.byref(b))
+        return int(a.value), int(b.value)
+
+    def logits(self, out):
+        _check(lib().dg_indicator_logits(self._h, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+
+def n_features(dim, pde, N):
+    return int(lib().dg_mlp_features(dim, pde, N))
+
+
+class MLP:
+    """The learned indicator's network (see dg_mlp_create); inputs are CUDA tensors."""
+
+    def __init__(self, n_features, seed=0, stream=0):
+        self._h = ctypes.c_void_p()
+        _check(lib().dg_mlp_create(int(n_features), int(seed), ctypes.c_void_p(int(stream)), ctypes.byref(self._h)))
+        self.F = int(n_features)
+        self.P = int(lib().dg_mlp_param_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().dg_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.P, dtype=np.float32)
+        _check(lib().dg_mlp_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.P))
+        return out
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        assert a.size == self.P
+        _check(lib().dg_mlp_set_params(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.P))
+
+    def grad(self, X, y, pos_weight=1.0):
+        g = np.zeros(self.P, dtype=np.float32)
+        loss = ctypes.c_float(0)
+        _check(lib().dg_mlp_grad(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()), X.shape[0],
+                                 pos_weight, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def predict(self, X, out):
+        _check(lib().dg_mlp_predict(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0], ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def train_step(self, X, y, pos_weight=1.0, lr=1e-3, want_loss=False):
+        loss = ctypes.c_float(0)
+        _check(lib().dg_mlp_train_step(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       X.shape[0], pos_weight, lr, ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -36,6 +37,39 @@ void launch_scatter2(int pde, int N, const LaunchArgs& a, const double* lim, con
                      int nblocks);
 void launch_project2(int pde, int N, const LaunchArgs& a, const int* cell_inst, int kind, const double* params, int np);
 void launch_speed2(int pde, int N, const LaunchArgs& a, const int* cell_inst, double* out);
+int mlp_features(int dim, int pde, int N);
+int mlp_padded(int F);
+cudaError_t prepare_mlp(int dim, int pde, int N, int FP);
+void launch_features(int dim, int pde, int N, const LaunchArgs& a, double c0, float* X);
+void launch_label(int dim, int pde, int N, const LaunchArgs& a, double c0, const int* lc, const int* li,
+                  const Counters* cnt, const double* lim, float* label, int nblocks);
+void launch_mlp_fb(cudaStream_t st, const float* X, const unsigned char* y, long long B, int F, const float* params,
+                   float pw, float* h1, float* d1, float* h2, float* d2, float* dz, float* loss);
+void launch_mlp_wgrad(cudaStream_t st, const float* X, long long B, int F, const float* h1, const float* d1,
+                      const float* h2, const float* d2, const float* dz, float* grad);
+void launch_mlp_forward(cudaStream_t st, const float* X, long long B, int F, const float* params, float* z);
+void launch_mlp_adam(cudaStream_t st, float* params, const float* grad, float* m1, float* m2, int P, float lr, int t);
+void launch_mlp_export(cudaStream_t st, const float* params, int F, int FP, void* W1b, float* b1, void* W2b, float* b2,
+                       float* w3, float* b3);
+}  // namespace dg
+
+namespace dg {
+void launch_flag_mlp(int dim, int pde, int N, const LaunchArgs& a, double c0, const MlpInfer& W, unsigned char* flags,
+                     Counters* cnt, int* lc, int* li, float* logits);
+cudaError_t prepare_filter(int dim, int pde, int N, int FP);
+void launch_mlp_filter(int dim, int pde, int N, const LaunchArgs& a, double c0, const MlpInfer& W, const int* la_c,
+                       const int* la_i, const Counters* cnt_a, unsigned char* flags, Counters* cnt_b, int* lb_c,
+                       int* lb_i, int nblocks);
+void launch_scatter_save(int dim, int pde, int N, const LaunchArgs& a, const double* lim, double* save, const int* lc,
+                         const Counters* cnt, int nblocks);
+void launch_restore(int dim, int pde, int N, const LaunchArgs& a, const double* save, const int* lc, const int* li,
+                    const Counters* cnt, const unsigned int* fail, int nblocks);
+void launch_filter_inst(cudaStream_t st, const int* la_c, const int* la_i, const Counters* cnt_a,
+                        const unsigned int* fail, Counters* cnt_c, int* lc_c, int* lc_i, int nblocks);
+void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1,
+                            double gam, const int* lc, const int* li, const Counters* cnt, const unsigned char* flags,
+                            int skip_kept, unsigned int* fail, int nblocks);
+void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total);
 }  // namespace dg
 
 using namespace dg;
@@ -113,6 +147,19 @@ struct dg_mesh {
   double g_M = 0.0;
   int g_kernels = 0;
   std::vector<double> last_dt;
+  // learned indicator attached by dg_set_indicator_mlp: list B (TVB flags kept by the
+  // network), list C (fallback entries), saved unlimited modes, per-instance failure bits
+  void* mlp_buf = nullptr;
+  MlpInfer mlp{};
+  bool has_mlp = false;
+  int *lb_cell = nullptr, *lb_inst = nullptr, *lc_cell = nullptr, *lc_inst = nullptr;
+  Counters *cnt_b = nullptr, *cnt_c = nullptr;
+  double* save = nullptr;
+  unsigned int* fail = nullptr;              // [2][n_inst]: first and second screen
+  unsigned long long* pos_counts = nullptr;  // [0] fallbacks, [1] failures after the fallback
+  bool use_b = false;                        // dg_cswenolimit limits list B (learned) or A (TVB)
+  unsigned long long* flag_totals = nullptr;  // TVB-flagged, limited, passes (dg_step)
+  double psi_q[16], psi_p1[4];
 };
 
 static size_t mesh_doubles(const dg_mesh* m) { return (size_t)m->ncell * m->V * m->NP; }
@@ -134,6 +181,10 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->list_inst);
   cudaFree(m->cnt);
   cudaFree(m->d_speed);
+  cudaFree(m->flag_totals);
+  cudaFree(m->mlp_buf);
+  cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
+  cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->save); cudaFree(m->fail); cudaFree(m->pos_counts);
   delete m;
   return DG_OK;
 }
@@ -202,7 +253,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->U[1], plane) && alloc((void**)&m->U[2], plane) && alloc((void**)&m->lim, plane) &&
             alloc((void**)&m->flags, m->ctot) && alloc((void**)&m->list_cell, sizeof(int) * m->ctot) &&
             alloc((void**)&m->list_inst, sizeof(int) * m->ctot) && alloc((void**)&m->cnt, sizeof(Counters)) &&
-            alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst);
+            alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst) &&
+            alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long));
   if (!ok) {
     cudaGetLastError();
     dg_mesh_destroy(m);
@@ -213,6 +265,7 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (e == cudaSuccess) e = cudaMemcpy(m->d_cell_inst, cell_inst.data(), sizeof(int) * off, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->U[0], 0, plane);
   if (e == cudaSuccess) e = cudaMemset(m->cnt, 0, sizeof(Counters));
+  if (e == cudaSuccess) e = cudaMemset(m->flag_totals, 0, 3 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     dg_mesh_destroy(m);
     return fail(DG_ECUDA, "mesh upload: %s", cudaGetErrorString(e));
@@ -256,23 +309,96 @@ static void k_stage(dg_mesh* m, int stage, int in, int out, double dt_all) {
   m->launches++;
 }
 
+// U_0 -> cell mean factor: psi_0 in 1D, psi_0^2 in 2D
+static double mean_factor(const dg_mesh* m) { return m->dim == 1 ? g_tabs[0].psi_0[0] : g_tabs[0].psi_0[0] * g_tabs[0].psi_0[0]; }
+
+// every cell's logit (diagnostics): the network on the whole mesh
+static void k_flag_learned(dg_mesh* m, float* logits) {
+  LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
+  launch_flag_mlp(m->dim, m->pde, m->N, a, mean_factor(m), m->mlp, m->flags, m->cnt, m->list_cell, m->list_inst, logits);
+  m->launches++;
+}
+
+static void k_flag(dg_mesh* m, double M);
+static void k_limit_list(dg_mesh* m, const int* lc, const int* li, const Counters* cnt);
+
+// the learned indicator: TVB flags (list A), then the network keeps a subset (list B)
+static cudaError_t learned_flags(dg_mesh* m, double M) {
+  cudaError_t e = cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->cnt_b, 0, sizeof(Counters), m->st);
+  if (e != cudaSuccess) return e;
+  k_flag(m, M);
+  LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
+  launch_mlp_filter(m->dim, m->pde, m->N, a, mean_factor(m), m->mlp, m->list_cell, m->list_inst, m->cnt, m->flags,
+                    m->cnt_b, m->lb_cell, m->lb_inst, m->limit_blocks);
+  m->launches++;
+  return cudaSuccess;
+}
+
+// limiter on list B with the positivity fallback of the learned indicator (Euler).  Only
+// the cells the network skipped (TVB-flagged, not kept) differ from what the plain method
+// would produce from this stage, so only they are screened; a failing instance gets its
+// unlimited modes back and is limited with the TVB list, exactly as the plain method
+// would; a second screen of those cells counts the instances that still fail.
+static cudaError_t learned_limit(dg_mesh* m) {
+  LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
+  if (m->pde != DG_EULER) {
+    k_limit_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
+    return cudaSuccess;
+  }
+  unsigned int* fail2 = m->fail + m->n_inst;
+  cudaError_t e = cudaMemsetAsync(m->fail, 0, 2 * sizeof(unsigned int) * m->n_inst, m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->cnt_c, 0, sizeof(Counters), m->st);
+  if (e != cudaSuccess) return e;
+  if (m->dim == 1) launch_limit1(m->pde, m->N, a, m->lb_cell, m->lb_inst, m->cnt_b, m->lim, m->limit_blocks);
+  else launch_limit2(m->pde, m->N, a, m->lb_cell, m->lb_inst, m->cnt_b, m->lim, m->limit_blocks);
+  launch_scatter_save(m->dim, m->pde, m->N, a, m->lim, m->save, m->lb_cell, m->cnt_b, m->limit_blocks);
+  launch_positivity_list(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->list_cell, m->list_inst, m->cnt,
+                         m->flags, 1, m->fail, m->limit_blocks);
+  launch_count_fail(m->st, m->fail, m->n_inst, m->pos_counts);
+  launch_restore(m->dim, m->pde, m->N, a, m->save, m->lb_cell, m->lb_inst, m->cnt_b, m->fail, m->limit_blocks);
+  launch_filter_inst(m->st, m->list_cell, m->list_inst, m->cnt, m->fail, m->cnt_c, m->lc_cell, m->lc_inst,
+                     m->limit_blocks);
+  k_limit_list(m, m->lc_cell, m->lc_inst, m->cnt_c);
+  launch_positivity_list(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->lc_cell, m->lc_inst, m->cnt_c, m->flags,
+                         0, fail2, m->limit_blocks);
+  launch_count_fail(m->st, fail2, m->n_inst, m->pos_counts + 1);
+  m->launches += 9;
+  return cudaSuccess;
+}
+
 static void k_flag(dg_mesh* m, double M) {
   if (m->dim == 1) launch_flag1(m->pde, m->N, args<LaunchArgs>(m, 0, m->cur, m->cur), M, m->flags, m->cnt, m->list_cell, m->list_inst);
   else launch_flag2(m->pde, m->N, args<LaunchArgs>(m, 0, m->cur, m->cur), M, m->flags, m->cnt, m->list_cell, m->list_inst);
   m->launches++;
 }
 
-static void k_limit(dg_mesh* m) {
+static void k_limit_list(dg_mesh* m, const int* lc, const int* li, const Counters* cnt) {
+  auto a = args<LaunchArgs>(m, 0, m->cur, m->cur);
   if (m->dim == 1) {
-    auto a = args<LaunchArgs>(m, 0, m->cur, m->cur);
-    launch_limit1(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
-    launch_scatter1(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
+    launch_limit1(m->pde, m->N, a, lc, li, cnt, m->lim, m->limit_blocks);
+    launch_scatter1(m->pde, m->N, a, m->lim, lc, cnt, m->limit_blocks);
   } else {
-    auto a = args<LaunchArgs>(m, 0, m->cur, m->cur);
-    launch_limit2(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
-    launch_scatter2(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
+    launch_limit2(m->pde, m->N, a, lc, li, cnt, m->lim, m->limit_blocks);
+    launch_scatter2(m->pde, m->N, a, m->lim, lc, cnt, m->limit_blocks);
   }
   m->launches += 2;
+}
+
+static void k_limit(dg_mesh* m) {
+  if (m->use_b) k_limit_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
+  else k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
+}
+
+// Adds the TVB list length and the limited list length of one pass to running totals
+// (extra: the fallback list of the learned indicator, whose cells are limited as well).
+static __global__ void k_accum_flags(const Counters* __restrict__ tvb, const Counters* __restrict__ limited,
+                                     const Counters* __restrict__ extra, unsigned long long* __restrict__ totals) {
+  if (threadIdx.x == 0) {
+    totals[0] += tvb->n_flag;
+    totals[1] += limited->n_flag + (extra ? extra->n_flag : 0u);
+    totals[2] += 1;
+  }
 }
 
 // ----------------------------------------------------------------------------- layout
@@ -387,18 +513,27 @@ extern "C" dg_status dg_rk_stage(dg_mesh* m, int stage, double dt) {
 extern "C" dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flagged, int64_t* n_near,
                                    uint8_t* flags_out) {
   if (!m) return fail(DG_EINVAL, "null mesh");
-  if (indicator != DG_IND_TVB) return fail(DG_EINVAL, "indicator %d is not available", indicator);
+  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP) return fail(DG_EINVAL, "unknown indicator %d", indicator);
+  if (indicator == DG_IND_MLP && !m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
   if (!(tvb_M >= 0.0)) return fail(DG_EINVAL, "tvb_M must be >= 0");
-  CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
-  k_flag(m, tvb_M);
+  if (indicator == DG_IND_MLP) {
+    CK(learned_flags(m, tvb_M));
+  } else {
+    CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+    k_flag(m, tvb_M);
+  }
   CK(cudaGetLastError());
   m->flags_valid = true;
+  m->use_b = indicator == DG_IND_MLP;
   if (n_flagged || n_near || flags_out) {
-    Counters c;
+    Counters c, cb;
     CK(cudaMemcpyAsync(&c, m->cnt, sizeof(c), cudaMemcpyDeviceToHost, m->st));
+    if (m->use_b) {
+      CK(cudaMemcpyAsync(&cb, m->cnt_b, sizeof(cb), cudaMemcpyDeviceToHost, m->st));
+    }
     if (flags_out) CK(cudaMemcpyAsync(flags_out, m->flags, m->ncell, cudaMemcpyDeviceToHost, m->st));
     CK(cudaStreamSynchronize(m->st));
-    if (n_flagged) *n_flagged = c.n_flag;
+    if (n_flagged) *n_flagged = m->use_b ? cb.n_flag : c.n_flag;
     if (n_near) *n_near = c.n_near;
   }
   return DG_OK;
@@ -426,14 +561,22 @@ extern "C" dg_status dg_max_wavespeed(dg_mesh* m, double* out) {
 }
 
 // The three (stage, indicator, limiter) passes of one SSP-RK3 step, enqueued on m->st.
-static dg_status enqueue_step(dg_mesh* m, double M) {
+static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
   for (int s = 1; s <= 3; ++s) {
     const int in = s == 1 ? 0 : m->cur, out = stage_out(s);
     k_stage(m, s, in, out, 0.0);
     m->cur = out;
-    CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
-    k_flag(m, M);
-    k_limit(m);
+    if (indicator == DG_IND_MLP) {
+      CK(learned_flags(m, M));
+      CK(learned_limit(m));
+      k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt_b, m->pde == DG_EULER ? m->cnt_c : nullptr, m->flag_totals);
+    } else {
+      CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+      k_flag(m, M);
+      k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
+      k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt, nullptr, m->flag_totals);
+    }
+    m->launches++;
   }
   CK(cudaGetLastError());
   return DG_OK;
@@ -441,7 +584,8 @@ static dg_status enqueue_step(dg_mesh* m, double M) {
 
 extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M) {
   if (!m) return fail(DG_EINVAL, "null mesh");
-  if (indicator != DG_IND_TVB) return fail(DG_EINVAL, "indicator %d is not available", indicator);
+  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP) return fail(DG_EINVAL, "unknown indicator %d", indicator);
+  if (indicator == DG_IND_MLP && !m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
   if (m->last_stage != 0 && m->last_stage != 3) return fail(DG_ESTATE, "a step was left unfinished (stage %d)", m->last_stage);
   // the graph reads the per-instance time steps from device memory
   if (dt > 0.0) {
@@ -458,7 +602,7 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
   }
   m->cur = 0;
   if (m->st == nullptr) {  // the legacy default stream cannot be captured
-    dg_status s = enqueue_step(m, tvb_M);
+    dg_status s = enqueue_step(m, indicator, tvb_M);
     m->last_stage = 3;
     m->flags_valid = false;
     return s;
@@ -471,7 +615,7 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
     cudaGraph_t graph;
     const long long before = m->launches;
     CK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
-    dg_status s = enqueue_step(m, tvb_M);
+    dg_status s = enqueue_step(m, indicator, tvb_M);
     cudaError_t e = cudaStreamEndCapture(m->st, &graph);
     if (s != DG_OK) return s;
     if (e != cudaSuccess) return fail(DG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -512,5 +656,278 @@ extern "C" dg_status dg_limiter_tables(int N, double* rp, double* rw, double* C,
       for (int l = 0; l < N1; ++l) B[(i * N1 + k) * N1 + l] = t.B[i][k][l];
   for (int k = 0; k < 2 * N + 1; ++k)
     for (int n = 0; n < N1; ++n) SA[k * N1 + n] = t.SA[k][n];
+  return DG_OK;
+}
+
+// ----------------------------------------------------------------------------- learned indicator
+struct dg_mlp {
+  int F = 0, FP = 0, P = 0, t = 0;
+  cudaStream_t st = nullptr;
+  float *params = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *loss = nullptr;
+  void* infer = nullptr;  // BF16 W1 [32][FP], BF16 W2 [32][32], FP32 b1, b2, w3, b3
+  long long cap = 0;
+  float *h1 = nullptr, *d1 = nullptr, *h2 = nullptr, *d2 = nullptr, *dz = nullptr;
+};
+
+static const int kHidden = 32;
+
+static size_t infer_bytes(int FP) { return 2 * (size_t)kHidden * FP + 2 * kHidden * kHidden + 4 * (3 * kHidden + 4); }
+
+static MlpInfer infer_view(void* buf, int FP, float tau) {
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  MlpInfer w{};
+  w.W1 = p;
+  w.W2 = p + 2 * (size_t)kHidden * FP;
+  float* f = reinterpret_cast<float*>(p + 2 * (size_t)kHidden * FP + 2 * kHidden * kHidden);
+  w.b1 = f;
+  w.b2 = f + kHidden;
+  w.w3 = f + 2 * kHidden;
+  w.b3 = f + 3 * kHidden;
+  w.FP = FP;
+  w.tau = tau;
+  return w;
+}
+
+static void mlp_export(dg_mlp* n) {
+  MlpInfer w = infer_view(n->infer, n->FP, 0.f);
+  launch_mlp_export(n->st, n->params, n->F, n->FP, const_cast<void*>(w.W1), const_cast<float*>(w.b1),
+                    const_cast<void*>(w.W2), const_cast<float*>(w.b2), const_cast<float*>(w.w3),
+                    const_cast<float*>(w.b3));
+}
+
+extern "C" int dg_mlp_features(int dim, int pde, int N) {
+  if ((dim != 1 && dim != 2) || (pde != 0 && pde != 1) || N < 1 || N > 3) return -1;
+  return mlp_features(dim, pde, N);
+}
+
+extern "C" size_t dg_mlp_param_count(const dg_mlp* n) { return n ? (size_t)n->P : 0; }
+
+extern "C" dg_status dg_mlp_destroy(dg_mlp* n) {
+  if (!n) return DG_OK;
+  cudaFree(n->params); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2); cudaFree(n->loss); cudaFree(n->infer);
+  cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz);
+  delete n;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_create(int n_features, uint64_t seed, void* stream, dg_mlp** out) {
+  if (!out) return fail(DG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_features < 1 || n_features > 4096) return fail(DG_EINVAL, "bad feature count %d", n_features);
+  dg_mlp* n = new (std::nothrow) dg_mlp();
+  if (!n) return fail(DG_ENOMEM, "host allocation");
+  n->F = n_features;
+  n->FP = mlp_padded(n_features);
+  n->P = kHidden * n_features + kHidden + kHidden * kHidden + kHidden + kHidden + 1;
+  n->st = (cudaStream_t)stream;
+  const size_t pb = sizeof(float) * n->P;
+  if (cudaMalloc(&n->params, pb) != cudaSuccess || cudaMalloc(&n->grad, pb) != cudaSuccess ||
+      cudaMalloc(&n->m1, pb) != cudaSuccess || cudaMalloc(&n->m2, pb) != cudaSuccess ||
+      cudaMalloc(&n->loss, sizeof(float)) != cudaSuccess || cudaMalloc(&n->infer, infer_bytes(n->FP)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_mlp_destroy(n);
+    return fail(DG_ENOMEM, "device allocation for the network");
+  }
+  // He-uniform initial weights from a splitmix64 stream, zero biases
+  std::vector<float> h(n->P, 0.0f);
+  uint64_t x = seed;
+  auto uni = [&]() {
+    x += 0x9e3779b97f4a7c15ULL;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const double a1 = std::sqrt(6.0 / n_features), a2 = std::sqrt(6.0 / kHidden);
+  size_t o = 0;
+  for (int i = 0; i < kHidden * n_features; ++i) h[o++] = (float)((2 * uni() - 1) * a1);
+  o += kHidden;
+  for (int i = 0; i < kHidden * kHidden; ++i) h[o++] = (float)((2 * uni() - 1) * a2);
+  o += kHidden;
+  for (int i = 0; i < kHidden; ++i) h[o++] = (float)((2 * uni() - 1) * a2);
+  cudaError_t e = cudaMemcpy(n->params, h.data(), pb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->m1, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(n->m2, 0, pb);
+  if (e != cudaSuccess) {
+    dg_mlp_destroy(n);
+    return fail(DG_ECUDA, "network upload: %s", cudaGetErrorString(e));
+  }
+  mlp_export(n);
+  *out = n;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_get_params(dg_mlp* n, float* out, size_t count) {
+  if (!n || !out) return fail(DG_EINVAL, "null argument");
+  if (count != (size_t)n->P) return fail(DG_EINVAL, "parameter count %zu != %d", count, n->P);
+  CK(cudaMemcpyAsync(out, n->params, sizeof(float) * n->P, cudaMemcpyDeviceToHost, n->st));
+  CK(cudaStreamSynchronize(n->st));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_set_params(dg_mlp* n, const float* in, size_t count) {
+  if (!n || !in) return fail(DG_EINVAL, "null argument");
+  if (count != (size_t)n->P) return fail(DG_EINVAL, "parameter count %zu != %d", count, n->P);
+  CK(cudaMemcpyAsync(n->params, in, sizeof(float) * n->P, cudaMemcpyHostToDevice, n->st));
+  CK(cudaMemsetAsync(n->m1, 0, sizeof(float) * n->P, n->st));
+  CK(cudaMemsetAsync(n->m2, 0, sizeof(float) * n->P, n->st));
+  n->t = 0;
+  mlp_export(n);
+  CK(cudaStreamSynchronize(n->st));
+  return DG_OK;
+}
+
+static dg_status mlp_backward(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pw) {
+  if (B > n->cap) {
+    cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz);
+    n->h1 = n->d1 = n->h2 = n->d2 = n->dz = nullptr;
+    const size_t hb = sizeof(float) * kHidden * (size_t)B;
+    if (cudaMalloc(&n->h1, hb) != cudaSuccess || cudaMalloc(&n->d1, hb) != cudaSuccess ||
+        cudaMalloc(&n->h2, hb) != cudaSuccess || cudaMalloc(&n->d2, hb) != cudaSuccess ||
+        cudaMalloc(&n->dz, sizeof(float) * (size_t)B) != cudaSuccess) {
+      cudaGetLastError();
+      n->cap = 0;
+      return fail(DG_ENOMEM, "training scratch for %lld samples", (long long)B);
+    }
+    n->cap = B;
+  }
+  CK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->P, n->st));
+  CK(cudaMemsetAsync(n->loss, 0, sizeof(float), n->st));
+  launch_mlp_fb(n->st, X, y, B, n->F, n->params, pw, n->h1, n->d1, n->h2, n->d2, n->dz, n->loss);
+  launch_mlp_wgrad(n->st, X, B, n->F, n->h1, n->d1, n->h2, n->d2, n->dz, n->grad);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_grad(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pos_weight,
+                                 float* grad_out, float* loss_out) {
+  if (!n || !X || !y || B < 1) return fail(DG_EINVAL, "bad arguments");
+  dg_status s = mlp_backward(n, X, y, B, pos_weight);
+  if (s != DG_OK) return s;
+  if (grad_out) CK(cudaMemcpyAsync(grad_out, n->grad, sizeof(float) * n->P, cudaMemcpyDeviceToHost, n->st));
+  if (loss_out) CK(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
+  CK(cudaStreamSynchronize(n->st));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_train_step(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pos_weight,
+                                       float lr, float* loss_out) {
+  if (!n || !X || !y || B < 1 || !(lr > 0.f)) return fail(DG_EINVAL, "bad arguments");
+  dg_status s = mlp_backward(n, X, y, B, pos_weight);
+  if (s != DG_OK) return s;
+  n->t += 1;
+  launch_mlp_adam(n->st, n->params, n->grad, n->m1, n->m2, n->P, lr, n->t);
+  mlp_export(n);
+  CK(cudaGetLastError());
+  if (loss_out) {
+    CK(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
+    CK(cudaStreamSynchronize(n->st));
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_predict(dg_mlp* n, const float* X, int64_t B, float* logits) {
+  if (!n || !X || !logits || B < 1) return fail(DG_EINVAL, "bad arguments");
+  launch_mlp_forward(n->st, X, B, n->F, n->params, logits);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau) {
+  if (!m || !n) return fail(DG_EINVAL, "null argument");
+  const int F = mlp_features(m->dim, m->pde, m->N);
+  if (F != n->F) return fail(DG_EINVAL, "network has %d features, this mesh needs %d", n->F, F);
+  if (!m->mlp_buf) {
+    const size_t plane = (size_t)m->ctot * m->V * m->NP * sizeof(double);
+    bool ok = cudaMalloc(&m->mlp_buf, infer_bytes(n->FP)) == cudaSuccess &&
+              cudaMalloc(&m->lb_cell, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->lb_inst, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->lc_cell, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->lc_inst, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->cnt_b, sizeof(Counters)) == cudaSuccess &&
+              cudaMalloc(&m->cnt_c, sizeof(Counters)) == cudaSuccess &&
+              (m->pde != DG_EULER || cudaMalloc(&m->save, plane) == cudaSuccess) &&
+              cudaMalloc(&m->fail, 2 * sizeof(unsigned int) * m->n_inst) == cudaSuccess &&
+              cudaMalloc(&m->pos_counts, 2 * sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return fail(DG_ENOMEM, "device allocation for the learned indicator");
+    }
+    CK(cudaMemset(m->pos_counts, 0, 2 * sizeof(unsigned long long)));
+    CK(cudaMemset(m->cnt_b, 0, sizeof(Counters)));
+    CK(prepare_mlp(m->dim, m->pde, m->N, n->FP));
+    CK(prepare_filter(m->dim, m->pde, m->N, n->FP));
+    const dgt::Tabs& tb = g_tabs[m->N - 1];
+    for (int q = 0; q <= m->N; ++q)
+      for (int k = 0; k <= m->N; ++k) m->psi_q[q * (m->N + 1) + k] = tb.psi_q[q][k];
+    for (int k = 0; k <= m->N; ++k) m->psi_p1[k] = tb.psi_p1[k];
+  }
+  // the network's stream must have finished its last update before the copy
+  CK(cudaStreamSynchronize(n->st));
+  CK(cudaMemcpyAsync(m->mlp_buf, n->infer, infer_bytes(n->FP), cudaMemcpyDeviceToDevice, m->st));
+  m->mlp = infer_view(m->mlp_buf, n->FP, tau);
+  m->has_mlp = true;
+  if (m->gexec && m->g_ind == DG_IND_MLP) {  // the threshold is a kernel argument of the graph
+    cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_flag_statistics(dg_mesh* m, int64_t* tvb_flagged, int64_t* limited, int64_t* passes,
+                                        int reset) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  unsigned long long c[3];
+  CK(cudaMemcpyAsync(c, m->flag_totals, sizeof(c), cudaMemcpyDeviceToHost, m->st));
+  if (reset) CK(cudaMemsetAsync(m->flag_totals, 0, sizeof(c), m->st));
+  CK(cudaStreamSynchronize(m->st));
+  if (tvb_flagged) *tvb_flagged = (int64_t)c[0];
+  if (limited) *limited = (int64_t)c[1];
+  if (passes) *passes = (int64_t)c[2];
+  return DG_OK;
+}
+
+extern "C" dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  unsigned long long c[2] = {0, 0};
+  if (m->pos_counts) {
+    CK(cudaMemcpyAsync(c, m->pos_counts, sizeof(c), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaStreamSynchronize(m->st));
+  }
+  if (fallbacks) *fallbacks = (int64_t)c[0];
+  if (failures) *failures = (int64_t)c[1];
+  return c[1] ? DG_EPOSITIVITY : DG_OK;
+}
+
+extern "C" dg_status dg_indicator_logits(dg_mesh* m, float* logits) {
+  if (!m || !logits) return fail(DG_EINVAL, "null argument");
+  if (!m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
+  CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+  k_flag_learned(m, logits);
+  CK(cudaGetLastError());
+  m->flags_valid = true;
+  m->use_b = false;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* change) {
+  if (!m || !X || !flags || !change) return fail(DG_EINVAL, "null argument");
+  LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
+  const double c0 = mean_factor(m);
+  m->use_b = false;
+  launch_features(m->dim, m->pde, m->N, a, c0, X);
+  CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+  k_flag(m, tvb_M);
+  CK(cudaMemsetAsync(change, 0, sizeof(float) * m->ncell, m->st));
+  if (m->dim == 1) launch_limit1(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
+  else launch_limit2(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
+  launch_label(m->dim, m->pde, m->N, a, c0, m->list_cell, m->list_inst, m->cnt, m->lim, change, m->limit_blocks);
+  CK(cudaMemcpyAsync(flags, m->flags, m->ncell, cudaMemcpyDeviceToDevice, m->st));
+  if (m->dim == 1) launch_scatter1(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
+  else launch_scatter2(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
+  m->launches += 4;
+  CK(cudaGetLastError());
+  m->flags_valid = false;
   return DG_OK;
 }

@@ -19,6 +19,19 @@ struct LaunchArgs {
   double gam;
 };
 
+// Inference weights of the learned indicator (device pointers): W1 BF16 [32][FP] (rows
+// padded with zeros to FP columns), b1 FP32 [32], W2 BF16 [32][32], b2, w3 FP32 [32], b3.
+struct MlpInfer {
+  const void* W1;
+  const float* b1;
+  const void* W2;
+  const float* b2;
+  const float* w3;
+  const float* b3;
+  int FP;
+  float tau;
+};
+
 // Per-call device counters (one struct per mesh, zeroed before each indicator pass).
 struct Counters {
   unsigned int n_flag;   // number of troubled cells in the list

@@ -299,4 +299,4 @@ def test_call_order_errors_and_launch_count():
         before = g.launches
         g.step(1e-4)
     torch.cuda.synchronize()
-    assert g.launches - before == 12  # 3 x (stage, flags, limiter, scatter)
+    assert g.launches - before == 15  # 3 x (stage, flags, limiter, scatter, statistics)
