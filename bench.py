@@ -236,7 +236,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--workload", default="quadrant", choices=["quadrant", "burgers_batched", "euler_batched_p3"],
+                    help="quadrant: 2D Euler P2 four-quadrant problem (size^2, learned vs plain); "
+                         "burgers_batched: 64 2D Burgers P2 instances (64^2..512^2); "
+                         "euler_batched_p3: 256 2D Euler P3 four-quadrant instances (128^2..1024^2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arms", default="both", choices=["both", "plain"],
+                    help="plain: time only the TVB indicator (no training; for profiling runs)")
     ap.add_argument("--clocks-out", default=None)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -250,6 +256,8 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.workload != "quadrant":
+        return batched_arm(args, dist, rank, world, torch, dgl)
     n = args.size
     w = W.euler_2d_quadrant(n, 2)
     st = torch.cuda.Stream()
@@ -258,8 +266,10 @@ def main():
     # and calibrated with the library's kernels (untimed)
     from paper_1904_11147_gb300 import train as T
     t_train = time.perf_counter()
-    with torch.cuda.stream(st):
-        net, tau, tinfo = T.train_indicator(stream=st)
+    net, tau, tinfo = None, 0.0, {"val_recall": None, "tol": None, "val_predicted": 0, "val_tvb_flagged": 1}
+    if args.arms == "both":
+        with torch.cuda.stream(st):
+            net, tau, tinfo = T.train_indicator(stream=st)
     st.synchronize()
     t_train = time.perf_counter() - t_train
 
@@ -273,6 +283,7 @@ def main():
     mesh = make_mesh(False)
     ws = mesh.max_wavespeed()[0]
     dt = 0.1 / (ws[0] * n + ws[1] * n)
+    tune = mesh.autotune(dt)  # stage tile height and limiter grid, measured here (untimed)
     dofs = mesh.size
     u0 = torch.empty(dofs, dtype=torch.float64, device="cuda")
     mesh.get_modes(u0)
@@ -302,10 +313,15 @@ def main():
         return ms_, launches_, clk, tvbf / max(passes, 1) / (n * n), limited / max(passes, 1) / (n * n)
 
     with torch.cuda.stream(st):
-        ms_plain, _, clk_plain, tvb_frac, lim_plain = timed_arm(mesh, dgl.IND_TVB, None)
-        lmesh = make_mesh(True)
-        ms, launches, clk, _, lim_learned = timed_arm(lmesh, dgl.IND_MLP, args.clocks_out)
-        fallbacks, failures = lmesh.positivity_report()
+        if args.arms == "both":
+            ms_plain, _, clk_plain, tvb_frac, lim_plain = timed_arm(mesh, dgl.IND_TVB, None)
+            lmesh = make_mesh(True)
+            ind_main = dgl.IND_MLP
+            ms, launches, clk, _, lim_learned = timed_arm(lmesh, ind_main, args.clocks_out)
+            fallbacks, failures = lmesh.positivity_report()
+        else:
+            ms_plain, launches, clk_plain, tvb_frac, lim_plain = timed_arm(mesh, dgl.IND_TVB, args.clocks_out)
+            lmesh, ind_main, ms, clk, lim_learned, fallbacks, failures = mesh, dgl.IND_TVB, ms_plain, clk_plain, lim_plain, 0, 0
         value = dofs * args.steps * world / (ms / 1e3)
         value_plain = dofs * args.steps * world / (ms_plain / 1e3)
 
@@ -330,7 +346,7 @@ def main():
         host_in.copy_(u0.cpu())
         for _ in range(2):
             lmesh.set_modes(host_in)
-            lmesh.step(dt, dgl.IND_MLP)
+            lmesh.step(dt, ind_main)
             lmesh.get_modes(host_out)
         barrier(dist)
         torch.cuda.synchronize()
@@ -341,7 +357,7 @@ def main():
         k_e2e = max(3, args.steps // 2)
         for _ in range(k_e2e):
             lmesh.set_modes(host_in)
-            lmesh.step(dt, dgl.IND_MLP)
+            lmesh.step(dt, ind_main)
             lmesh.get_modes(host_out)
         e3.record(st)
         e3.synchronize()
@@ -374,8 +390,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt, "indicator": "learned (TVB-gated MLP)",
+        "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt,
+                   "indicator": "learned (TVB-gated MLP)" if args.arms == "both" else "tvb",
                    "tvb_M": 0.01, "limiter": "cswenolimit", "graph": True,
+                   "autotuned": {"stage_tile_rows": tune[0], "limiter_blocks_per_sm": tune[1]},
                    "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "learned": {"value": value, "ms_per_step": ms / args.steps, "limited_fraction": lim_learned, "tau": tau,
@@ -399,6 +417,59 @@ def main():
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def batched_arm(args, dist, rank, world, torch, dgl):
+    """Batched workloads: many uneven instances in one mesh, per-instance time steps (CFL
+    0.1), plain TVB indicator, steps replayed from the CUDA graph."""
+    if args.workload == "burgers_batched":
+        w = W.burgers_2d_batched()
+    else:
+        w = W.euler_2d_batched()
+    st = torch.cuda.Stream()
+    m = dgl.Mesh(2, w.pde, w.N, w.nx, w.ny, w.box, bc=w.bc, stream=st.cuda_stream)
+    m.project_ic(w.ic, w.params)
+    ws = m.max_wavespeed()
+    dts = []
+    for i in range(w.n_inst):
+        hx = (w.box[i][1] - w.box[i][0]) / w.nx[i]
+        hy = (w.box[i][3] - w.box[i][2]) / w.ny[i]
+        dts.append(0.1 / (ws[i, 0] / hx + ws[i, 1] / hy))
+    m.set_dt(dts)
+    tune = m.autotune(min(dts))
+    m.set_dt(dts)
+    with torch.cuda.stream(st):
+        for _ in range(args.warmup):
+            m.step(0.0)
+        st.synchronize()
+        m.flag_statistics(reset=True)
+        barrier(dist)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = m.launches
+        with ClockSampler(args.clocks_out) as clk:
+            e0.record(st)
+            for _ in range(args.steps):
+                m.step(0.0)
+            e1.record(st)
+            e1.synchronize()
+        ms = max_over_ranks(dist, e0.elapsed_time(e1))
+        launches = m.launches - l0
+    tvbf, limited, passes = m.flag_statistics()
+    if rank != 0:
+        return 0
+    dofs = m.size
+    value = dofs * args.steps * world / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "instances": w.n_inst, "cells": w.cells, "dofs": dofs, "indicator": "tvb",
+                       "limiter": "cswenolimit", "graph": True, "per_instance_dt": True,
+                       "autotuned": {"stage_tile_rows": tune[0], "limiter_blocks_per_sm": tune[1]},
+                       "limited_fraction": limited / max(passes, 1) / w.cells,
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": launches, "clocks": clk.summary()}
+    print(json.dumps(line))
     return 0
 
 

@@ -79,6 +79,8 @@ def lib():
             l.dg_flag_statistics.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
             l.dg_flag_statistics.restype = ctypes.c_int
+            l.dg_autotune.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            l.dg_autotune.restype = ctypes.c_int
             l.dg_indicator_logits.argtypes = [P, P]
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             for name in ("dg_mesh_create", "dg_mesh_destroy", "dg_set_modes", "dg_get_modes", "dg_project_ic",
@@ -223,6 +225,12 @@ class Mesh:
 
     def set_indicator(self, net, tau=0.0):
         _check(lib().dg_set_indicator_mlp(self._h, net._h, tau))
+
+    def autotune(self, dt):
+        """Chooses the stage tile height and the limiter grid on this mesh (see dg_autotune)."""
+        a, b = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().dg_autotune(self._h, dt, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     def flag_statistics(self, reset=False):
         """(TVB-flagged, limited, passes) totals over the dg_step limiter passes."""

@@ -1,6 +1,7 @@
 // C ABI of the library (include/dg.h): mesh management, host<->device layout changes,
 // the per-call entry points and the CUDA-graph time step.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cmath>
@@ -29,7 +30,7 @@ void launch_scatter1(int pde, int N, const LaunchArgs& a, const double* lim, con
                      int nblocks);
 void launch_project1(int pde, int N, const LaunchArgs& a, const int* cell_inst, int kind, const double* params, int np);
 void launch_speed1(int pde, int N, const LaunchArgs& a, const int* cell_inst, double* out);
-void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all);
+void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys);
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc, int* li);
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt, double* lim,
                    int nblocks);
@@ -140,6 +141,11 @@ struct dg_mesh {
   int last_stage = 0;   // 0: state is u^n; s: output of stage s
   bool flags_valid = false;
   int limit_blocks = 0;
+  int sms = 152;
+  // 2D stage tiles (TX x stage_ty cells), chosen by the autotuner
+  int stage_ty = 8;
+  Tile* d_stage_tiles = nullptr;
+  int n_stage_tiles = 0;
   long long launches = 0;
   // CUDA graph of one full step
   cudaGraphExec_t gexec = nullptr;
@@ -173,6 +179,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   if (m->gexec) cudaGraphExecDestroy(m->gexec);
   cudaFree(m->d_inst);
   cudaFree(m->d_tiles);
+  cudaFree(m->d_stage_tiles);
   cudaFree(m->d_cell_inst);
   for (auto& p : m->U) cudaFree(p);
   cudaFree(m->lim);
@@ -187,6 +194,64 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->save); cudaFree(m->fail); cudaFree(m->pos_counts);
   delete m;
   return DG_OK;
+}
+
+// ----------------------------------------------------------------------------- autotuning
+// Process-wide choices per (dim, pde, N, mesh-size class = floor(log2 cells)); optionally
+// loaded from and appended to the text file named by DG_AUTOTUNE_FILE
+// ("dim pde N class stage_ty limit_blocks_per_sm" per line).
+struct TuneKey {
+  int dim, pde, N, cls;
+  bool operator==(const TuneKey& o) const { return dim == o.dim && pde == o.pde && N == o.N && cls == o.cls; }
+};
+struct TuneVal {
+  int stage_ty, limit_per_sm;
+};
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+static bool g_tune_loaded = false;
+
+static int size_class(long long cells) {
+  int c = 0;
+  while ((1LL << (c + 1)) <= cells) ++c;
+  return c;
+}
+
+static void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = getenv("DG_AUTOTUNE_FILE");
+  if (!f) return;
+  FILE* fp = fopen(f, "r");
+  if (!fp) return;
+  TuneKey k;
+  TuneVal v;
+  while (fscanf(fp, "%d %d %d %d %d %d", &k.dim, &k.pde, &k.N, &k.cls, &v.stage_ty, &v.limit_per_sm) == 6)
+    if ((v.stage_ty == 4 || v.stage_ty == 8) && v.limit_per_sm >= 1 && v.limit_per_sm <= 64) g_tune.push_back({k, v});
+  fclose(fp);
+}
+
+static const TuneVal* tune_find(const TuneKey& k) {
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
+    if (it->first == k) return &it->second;
+  return nullptr;
+}
+
+// (re)builds the 2D stage tile list for tile height ty
+static cudaError_t build_stage_tiles(dg_mesh* m, int ty) {
+  std::vector<Tile> tiles;
+  for (int i = 0; i < m->n_inst; ++i) {
+    const Inst& I = m->h_inst[i];
+    for (int y0 = 0; y0 < I.ny; y0 += ty)
+      for (int x0 = 0; x0 < I.nx; x0 += tile_w2()) tiles.push_back(Tile{i, x0, y0, 0});
+  }
+  if (m->d_stage_tiles) cudaFree(m->d_stage_tiles);
+  m->d_stage_tiles = nullptr;
+  cudaError_t e = cudaMalloc(&m->d_stage_tiles, sizeof(Tile) * tiles.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(m->d_stage_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice);
+  m->n_stage_tiles = (int)tiles.size();
+  m->stage_ty = ty;
+  return e;
 }
 
 extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const int* nx, const int* ny,
@@ -270,16 +335,21 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
     dg_mesh_destroy(m);
     return fail(DG_ECUDA, "mesh upload: %s", cudaGetErrorString(e));
   }
-  if (dim == 2) {
-    e = prepare2(pde, N);
-    if (e != cudaSuccess) {
-      dg_mesh_destroy(m);
-      return fail(DG_ECUDA, "stage kernel attributes: %s", cudaGetErrorString(e));
-    }
-  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  m->limit_blocks = (sms > 0 ? sms : 152) * 8;
+  m->sms = sms > 0 ? sms : 152;
+  m->limit_blocks = m->sms * 8;
+  tune_load();
+  const TuneVal* tv = tune_find(TuneKey{dim, pde, N, size_class(off)});
+  if (tv) m->limit_blocks = m->sms * tv->limit_per_sm;
+  if (dim == 2) {
+    e = prepare2(pde, N);
+    if (e == cudaSuccess) e = build_stage_tiles(m, tv ? tv->stage_ty : 8);
+    if (e != cudaSuccess) {
+      dg_mesh_destroy(m);
+      return fail(DG_ECUDA, "stage kernel set-up: %s", cudaGetErrorString(e));
+    }
+  }
   *out = m;
   return DG_OK;
 }
@@ -304,10 +374,17 @@ static L args(dg_mesh* m, int un, int us, int out) {
 }
 
 static void k_stage(dg_mesh* m, int stage, int in, int out, double dt_all) {
-  if (m->dim == 1) launch_stage1(m->pde, m->N, args<LaunchArgs>(m, 0, in, out), stage, dt_all);
-  else launch_stage2(m->pde, m->N, args<LaunchArgs>(m, 0, in, out), stage, dt_all);
+  if (m->dim == 1) {
+    launch_stage1(m->pde, m->N, args<LaunchArgs>(m, 0, in, out), stage, dt_all);
+  } else {
+    LaunchArgs a = args<LaunchArgs>(m, 0, in, out);
+    a.tiles = m->d_stage_tiles;
+    a.ntiles = m->n_stage_tiles;
+    launch_stage2(m->pde, m->N, a, stage, dt_all, m->stage_ty);
+  }
   m->launches++;
 }
+
 
 // U_0 -> cell mean factor: psi_0 in 1D, psi_0^2 in 2D
 static double mean_factor(const dg_mesh* m) { return m->dim == 1 ? g_tabs[0].psi_0[0] : g_tabs[0].psi_0[0] * g_tabs[0].psi_0[0]; }
@@ -632,6 +709,83 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
   m->cur = 0;
   m->last_stage = 3;
   m->flags_valid = false;
+  return DG_OK;
+}
+
+// Times the candidate configurations on this mesh's current state (u^n is left unchanged):
+// the 2D stage tile height (4 or 8 rows) on stage 1, then the limiter's grid (2, 4, 8 or 16
+// blocks per SM) on the TVB-flagged cells of that stage.  The fastest are applied to the
+// mesh and remembered for meshes of the same kind and size class.
+extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm) {
+  if (!m || !(dt > 0.0)) return fail(DG_EINVAL, "bad arguments");
+  if (m->last_stage != 0 && m->last_stage != 3) return fail(DG_ESTATE, "a step was left unfinished");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](auto fn, int reps) -> float {
+    fn();  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(e0, m->st);
+      fn();
+      cudaEventRecord(e1, m->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = ms < best ? ms : best;
+    }
+    return best;
+  };
+  m->cur = 0;
+  int best_ty = m->stage_ty;
+  if (m->dim == 2) {
+    float best = 1e30f;
+    for (int ty : {8, 4}) {
+      cudaError_t e = build_stage_tiles(m, ty);
+      if (e != cudaSuccess) return fail(DG_ECUDA, "stage tiles: %s", cudaGetErrorString(e));
+      const float ms = time_it([&] { k_stage(m, 1, 0, 1, dt); }, 3);
+      if (ms < best) { best = ms; best_ty = ty; }
+    }
+    CK(build_stage_tiles(m, best_ty));
+  }
+  // limiter grid on the flagged cells of stage 1 (writes only the limiter scratch)
+  k_stage(m, 1, 0, 1, dt);
+  m->cur = 1;
+  CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+  k_flag(m, 0.01);
+  int best_mult = m->limit_blocks / m->sms;
+  {
+    float best = 1e30f;
+    for (int mult : {8, 2, 4, 16}) {
+      LaunchArgs a = args<LaunchArgs>(m, 0, 1, 1);
+      const float ms = time_it([&] {
+        if (m->dim == 1) launch_limit1(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->sms * mult);
+        else launch_limit2(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->sms * mult);
+      }, 3);
+      if (ms < best) { best = ms; best_mult = mult; }
+    }
+  }
+  m->limit_blocks = m->sms * best_mult;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  m->cur = 0;
+  m->last_stage = 0;
+  m->flags_valid = false;
+  if (m->gexec) {  // launch configurations are baked into the graph
+    cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+  }
+  const TuneKey k{m->dim, m->pde, m->N, size_class(m->ncell)};
+  g_tune.push_back({k, TuneVal{best_ty, best_mult}});
+  if (const char* f = getenv("DG_AUTOTUNE_FILE")) {
+    if (FILE* fp = fopen(f, "a")) {
+      fprintf(fp, "%d %d %d %d %d %d\n", k.dim, k.pde, k.N, k.cls, best_ty, best_mult);
+      fclose(fp);
+    }
+  }
+  if (stage_ty) *stage_ty = m->dim == 2 ? best_ty : 0;
+  if (limit_blocks_per_sm) *limit_blocks_per_sm = best_mult;
   return DG_OK;
 }
 

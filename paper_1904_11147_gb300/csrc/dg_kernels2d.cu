@@ -17,8 +17,7 @@ namespace dg {
 namespace k2 {
 
 constexpr int TX = 32;  // tile width = one warp
-constexpr int TY = 8;   // interior rows per tile
-constexpr int kStageThreads = (TY + 3) * 32;
+constexpr int TY = 8;   // rows per tile of the indicator and projection kernels
 
 // ----------------------------------------------------------------------------- tables
 template <int N>
@@ -251,32 +250,33 @@ __device__ __forceinline__ void trace_one(const double (&u)[V][NP], int dir, dou
 }
 
 // ----------------------------------------------------------------------------- stage
-// One tile of TX x TY cells per block.  Warps 0..TY-1 hold the interior rows, warp TY the
-// row below the tile, warp TY+1 the row above it, warp TY+2 the west (lanes 0..15) and
+// One tile of TX x TYS cells per block (TYS = 4 or 8, chosen by the autotuner).  Warps
+// 0..TYS-1 hold the interior rows, warp TYS the row below the tile, warp TYS+1 the row
+// above it, warp TYS+2 the west (lanes 0..15) and
 // east (lanes 16..31) halo cells, so that every trace and every face flux is computed
 // exactly once per tile by a full warp.
-template <int PDE, int N>
-__global__ void __launch_bounds__(kStageThreads, 1)
+template <int PDE, int N, int TYS>
+__global__ void __launch_bounds__((TYS + 3) * 32, 1)
     k_stage2(const double* __restrict__ un, const double* __restrict__ us, double* __restrict__ out,
              const Inst* __restrict__ insts, const Tile* __restrict__ tiles, long long ctot, int bc, int stage,
              double dt_all, double gam) {
   using O = Off<N>;
   constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1, QV = Q * V;
-  // east traces, then x-face fluxes: [QV][TY][TX+1]; north traces, then y-face fluxes:
-  // [QV][TY+1][TX] (dynamic shared memory, above the 48 KB static limit for Euler P2/P3)
+  // east traces, then x-face fluxes: [QV][TYS][TX+1]; north traces, then y-face fluxes:
+  // [QV][TYS+1][TX] (dynamic shared memory, above the 48 KB static limit for Euler P2/P3)
   extern __shared__ double smem[];
   double* const sEb = smem;
-  double* const sNb = smem + QV * TY * (TX + 1);
-#define sE(qv, r, c) sEb[((qv) * TY + (r)) * (TX + 1) + (c)]
-#define sN(qv, r, c) sNb[((qv) * (TY + 1) + (r)) * TX + (c)]
+  double* const sNb = smem + QV * TYS * (TX + 1);
+#define sE(qv, r, c) sEb[((qv) * TYS + (r)) * (TX + 1) + (c)]
+#define sN(qv, r, c) sNb[((qv) * (TYS + 1) + (r)) * TX + (c)]
   const Tile tile = tiles[blockIdx.x];
   const Inst I = insts[tile.inst];
-  const int ncols = min(TX, I.nx - tile.x0), nrows = min(TY, I.ny - tile.y0);
+  const int ncols = min(TX, I.nx - tile.x0), nrows = min(TYS, I.ny - tile.y0);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double gm1 = gam - 1.0;
   const double sx = 2.0 / I.hx, sy = 2.0 / I.hy, ihx = 1.0 / I.hx, ihy = 1.0 / I.hy;
 
-  const bool interior = w < TY && w < nrows && lane < ncols;
+  const bool interior = w < TYS && w < nrows && lane < ncols;
   double acc[V][NP];
   double trW[Q][V], trS[Q][V];
   // ---------------------------------------------------------------- phase 1
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
           }
       }
     }
-  } else if (w == TY) {  // row below the tile: its north traces
+  } else if (w == TYS) {  // row below the tile: its north traces
     if (lane < ncols) {
       double u[V][NP], tN[Q][V];
       load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 - 1, bc, u);
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
 #pragma unroll
         for (int v = 0; v < V; ++v) sN(q * V + v, 0, lane) = tN[q][v];
     }
-  } else if (w == TY + 1) {  // row above the tile: its south traces (kept for phase 2)
+  } else if (w == TYS + 1) {  // row above the tile: its south traces (kept for phase 2)
     if (lane < ncols) {
       double u[V][NP];
       load_cell<V, NP>(us, ctot, I, tile.x0 + lane, tile.y0 + nrows, bc, u);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
           if (mode_b(m) & 1) u[v][m] = -u[v][m];
       trace_one<N>(u, 1, trS);
     }
-  } else if (w == TY + 2) {  // west halo (lanes < 16) east traces, east halo west traces
+  } else if (w == TYS + 2) {  // west halo (lanes < 16) east traces, east halo west traces
     const bool east = lane >= 16;
     const int row = east ? lane - 16 : lane;
     if (row < nrows) {
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
 #pragma unroll
       for (int v = 0; v < V; ++v) sN(q * V + v, w, lane) = fs[v];
     }
-  } else if (w == TY + 1) {
+  } else if (w == TYS + 1) {
     if (lane < ncols) {
       double uL[V], fs[V];
 #pragma unroll
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kStageThreads, 1)
         for (int v = 0; v < V; ++v) sN(q * V + v, nrows, lane) = fs[v];
       }
     }
-  } else if (w == TY + 2) {
+  } else if (w == TYS + 2) {
     const int row = lane - 16;
     if (lane >= 16 && row < nrows) {
       double uL[V], fs[V];
@@ -891,19 +891,22 @@ cudaError_t upload_tables2(const dgt::Tabs* tabs /* [3] for N = 1..3 */) {
     else { constexpr int P_ = 1, N_ = 3; CALL; } \
   } while (0)
 
-int stage_threads2() { return k2::kStageThreads; }
+int stage_threads2(int tys) { return (tys + 3) * 32; }
 
-template <int PDE, int N>
+template <int PDE, int N, int TYS>
 static size_t stage_smem2() {
   constexpr int QV = (N + 1) * nv_of(2, PDE);
-  return sizeof(double) * (size_t)(QV * k2::TY * (k2::TX + 1) + QV * (k2::TY + 1) * k2::TX);
+  return sizeof(double) * (size_t)(QV * TYS * (k2::TX + 1) + QV * (TYS + 1) * k2::TX);
 }
 
 template <int PDE, int N>
 static cudaError_t prep_stage2() {
   // opt in to more than 48 KB of dynamic shared memory (set per device, outside captures)
-  return cudaFuncSetAttribute(k2::k_stage2<PDE, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)stage_smem2<PDE, N>());
+  cudaError_t e = cudaFuncSetAttribute(k2::k_stage2<PDE, N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)stage_smem2<PDE, N, 8>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k2::k_stage2<PDE, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)stage_smem2<PDE, N, 4>());
 }
 
 cudaError_t prepare2(int pde, int N) {
@@ -912,17 +915,18 @@ cudaError_t prepare2(int pde, int N) {
   return e;
 }
 
-template <int PDE, int N>
+template <int PDE, int N, int TYS>
 static void run_stage2(const LaunchArgs& a, int stage, double dt_all) {
-  const size_t bytes = stage_smem2<PDE, N>();
-  k2::k_stage2<PDE, N><<<a.ntiles, k2::kStageThreads, bytes, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
-                                                                       a.bc, stage, dt_all, a.gam);
+  const size_t bytes = stage_smem2<PDE, N, TYS>();
+  k2::k_stage2<PDE, N, TYS><<<a.ntiles, (TYS + 3) * 32, bytes, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
+                                                                        a.bc, stage, dt_all, a.gam);
 }
 int tile_w2() { return k2::TX; }
 int tile_h2() { return k2::TY; }
 
-void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all) {
-  DG_DISPATCH2(pde, N, (run_stage2<P_, N_>(a, stage, dt_all)));
+void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys) {
+  if (tys == 4) DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 4>(a, stage, dt_all)));
+  else DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 8>(a, stage, dt_all)));
 }
 
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc,
