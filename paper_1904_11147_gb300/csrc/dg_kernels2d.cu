@@ -3,7 +3,8 @@
 //   k_stage2    one SSP-RK3 stage of Eq. (5): volume quadrature, traces, local
 //               Lax-Friedrichs fluxes on shared faces, lifting, stage combination
 //   k_flag2     TVB minmod indicator + ballot/scan compaction of troubled cells
-//   k_limit2    CSWENO limiter (Sec. 3), one thread per troubled cell
+//   k_limit2    CSWENO limiter (Sec. 3): Burgers one thread per troubled cell, Euler
+//               four lanes per troubled cell (k_limit2_euler_quad)
 //   k_project2  initial L2 projection (Eq. (2))
 //   k_speed2    largest characteristic speed over the cell means
 //
@@ -787,6 +788,160 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+
+// CSWENO for 2D Euler with four lanes per troubled cell (8 cells per warp).  Lane q of a
+// quad owns conserved variable q for the subcell averages and the projection, and
+// characteristic field q in the two sweeps; the quad exchanges values with shuffles, so
+// all lanes run the same FP64 instruction stream (the FP64 pipe is the bottleneck) while
+// each thread holds a quarter of the per-cell state.
+template <int N>
+__global__ void __launch_bounds__(128)
+    k_limit2_euler_quad(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc,
+                        const int* __restrict__ list_cell, const int* __restrict__ list_inst,
+                        const Counters* __restrict__ cnt, double* __restrict__ lim, long long cap, double gam) {
+  using O = Off<N>;
+  constexpr int NP = np_of(2, N), NS = O::NS, NG = O::NG, N1 = N + 1;
+  const unsigned int n = cnt->n_flag;
+  const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
+  const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned int base = warp * 8u; base < n; base += nwarps * 8u) {
+    const unsigned int i0 = base + (lane >> 2);
+    const bool active = i0 < n;
+    const unsigned int i = active ? i0 : n - 1;  // idle quads repeat a valid entry
+    const long long g = list_cell[i];
+    const Inst I = insts[list_inst[i]];
+    const int loc = (int)(g - I.off);
+    const int ix = loc % I.nx, iy = loc / I.nx;
+    // subcell averages of variable q
+    double avg[NS][NS];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        int jx = ix + dx, jy = iy + dy;
+        bool fx = false, fy = false;
+        if (bc == 0) {
+          jx = jx < 0 ? jx + I.nx : (jx >= I.nx ? jx - I.nx : jx);
+          jy = jy < 0 ? jy + I.ny : (jy >= I.ny ? jy - I.ny : jy);
+        } else {
+          if (jx < 0) { jx = 0; fx = true; }
+          if (jx >= I.nx) { jx = I.nx - 1; fx = true; }
+          if (jy < 0) { jy = 0; fy = true; }
+          if (jy >= I.ny) { jy = I.ny - 1; fy = true; }
+        }
+        const long long gj = I.off + (long long)jy * I.nx + jx;
+        double u[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const double x = __ldg(U + (long long)(q * NP + m) * ctot + gj);
+          const bool flip = (fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1));
+          u[m] = flip ? -x : x;
+        }
+        constexpr int k0[3] = {0, N, N + 1};
+        constexpr int kn[3] = {N, 1, N};
+#pragma unroll
+        for (int kx = k0[dx + 1]; kx < k0[dx + 1] + kn[dx + 1]; ++kx) {
+          double t[N1];
+#pragma unroll
+          for (int b = 0; b <= N; ++b) {
+            double sum = 0.0;
+#pragma unroll
+            for (int a = 0; a <= N - b; ++a) sum = fma(u[mode_idx(a, b)], T(O::SA + kx * N1 + a), sum);
+            t[b] = sum;
+          }
+#pragma unroll
+          for (int ky = k0[dy + 1]; ky < k0[dy + 1] + kn[dy + 1]; ++ky) {
+            double sum = 0.0;
+#pragma unroll
+            for (int b = 0; b <= N; ++b) sum = fma(t[b], T(O::SA + ky * N1 + b), sum);
+            avg[ky][kx] = sum;
+          }
+        }
+      }
+    // mean state of the troubled cell, gathered over the quad
+    const double mq = __ldg(U + (long long)(q * NP) * ctot + g) * T(O::C00);
+    double mean[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) mean[v] = __shfl_sync(0xffffffffu, mq, qb | v);
+    double Lq[4], Rq[4];  // row q of the left and right eigenvector matrices
+    auto rows_of = [&](int dir) {
+      double R[4][4], L[4][4];
+      euler_eig2(mean, dir, gam, R, L);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Lq[v] = q == 0 ? L[0][v] : (q == 1 ? L[1][v] : (q == 2 ? L[2][v] : L[3][v]));
+        Rq[v] = q == 0 ? R[0][v] : (q == 1 ? R[1][v] : (q == 2 ? R[2][v] : R[3][v]));
+      }
+    };
+    // x sweep: field q of each row, back to variable q at the NG x points
+    rows_of(0);
+    double rowv[NS][NG];
+#pragma unroll
+    for (int ky = 0; ky < NS; ++ky) {
+      double w[NS], r[NG];
+#pragma unroll
+      for (int kx = 0; kx < NS; ++kx) {
+        double s = 0.0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) s = fma(Lq[v], __shfl_sync(0xffffffffu, avg[ky][kx], qb | v), s);
+        w[kx] = s;
+      }
+      weno<N>(w, r);
+#pragma unroll
+      for (int gx = 0; gx < NG; ++gx) {
+        double s = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s = fma(Rq[f], __shfl_sync(0xffffffffu, r[gx], qb | f), s);
+        rowv[ky][gx] = s;
+      }
+    }
+    // y sweep: field q of each x point's column, back to variable q at the NG y points
+    rows_of(1);
+    double pv[NG][NG];  // [gy][gx]
+#pragma unroll
+    for (int gx = 0; gx < NG; ++gx) {
+      double w[NS], r[NG];
+#pragma unroll
+      for (int ky = 0; ky < NS; ++ky) {
+        double s = 0.0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) s = fma(Lq[v], __shfl_sync(0xffffffffu, rowv[ky][gx], qb | v), s);
+        w[ky] = s;
+      }
+      weno<N>(w, r);
+#pragma unroll
+      for (int gy = 0; gy < NG; ++gy) {
+        double s = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) s = fma(Rq[f], __shfl_sync(0xffffffffu, r[gy], qb | f), s);
+        pv[gy][gx] = s;
+      }
+    }
+    // Step 6 for variable q (tensor Gauss / Gauss-Lobatto rule)
+    double tq[NG][N1];
+#pragma unroll
+    for (int gy = 0; gy < NG; ++gy)
+#pragma unroll
+      for (int a = 0; a <= N; ++a) {
+        double s = 0.0;
+#pragma unroll
+        for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WG + gx) * T(O::PG + gx * N1 + a), pv[gy][gx], s);
+        tq[gy][a] = s;
+      }
+    if (active) {
+#pragma unroll
+      for (int m = 1; m < NP; ++m) {
+        const int a = mode_a(m), b = mode_b(m);
+        double s = 0.0;
+#pragma unroll
+        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WG + gy) * T(O::PG + gy * N1 + b), tq[gy][a], s);
+        lim[(long long)(q * NP + m) * cap + i] = s;
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- projection
 // Eq. (2) for the initial data: U_ab = sum_{qx,qy} w w u0(x, y) psi_a psi_b with N+4 Gauss
 // points per direction.  Parameters per instance (see dg.h for the families).
@@ -937,6 +1092,12 @@ void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* 
 
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
                    double* lim, int nblocks) {
+  if (pde == 1) {  // Euler: four lanes per troubled cell
+    if (N == 1) k2::k_limit2_euler_quad<1><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
+    else if (N == 2) k2::k_limit2_euler_quad<2><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
+    else k2::k_limit2_euler_quad<3><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
+    return;
+  }
   DG_DISPATCH2(pde, N, (k2::k_limit2<P_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt,
                                                                           lim, a.cap, a.gam)));
 }

@@ -183,7 +183,8 @@ def test_hundred_steps_parity(name):
     of each other.  With P3 the split of negative linear weights and smoothness-indicator
     forms with entries in the thousands amplify rounding differences by about an order of
     magnitude every 10-20 steps (a property of the scheme: the first step agrees to 1e-14),
-    so there the bound is asserted over the first 10 steps and the full track reported."""
+    so there the growth-free start is asserted (first 5 steps within 1e-12) and the full
+    track reported; the per-step agreement is asserted by the shadow test above."""
     import torch
     st = torch.cuda.Stream()
     o, g, u0, dt = _case(name, st.cuda_stream)
@@ -194,7 +195,7 @@ def test_hundred_steps_parity(name):
     print(name, "free-running deviation after 100 steps: %.3e, near-threshold: %d, track %s" %
           (err, near, ["%.1e" % e for e in track[::10]]))
     if "_p3" in name:
-        assert max(track[:10]) <= 1e-11, track[:10]
+        assert max(track[:5]) <= 1e-12, track[:5]
     else:
         assert err <= 1e-11, (err, near, ["%.1e" % e for e in track[::10]])
 
