@@ -133,13 +133,15 @@ dg_status dg_max_wavespeed(dg_mesh* m, double* out);
 /* Autotuner: times the candidate launch configurations on this mesh's current state with
  * the time step dt (u^n is left unchanged; stage buffers and limiter scratch are
  * overwritten): the 2D stage kernel's tile height (4 or 8 rows of 32 cells plus their
- * halo warps) and the limiter's grid (2, 4, 8 or 16 blocks per SM).  Applies the fastest
+ * halo warps) and launch form (one block per tile, or one persistent block per SM taking
+ * tiles from an atomic queue), and the limiter's grid (2, 4, 8 or 16 blocks per SM).
+ * Applies the fastest
  * to the mesh and remembers them for later meshes of the same dim, PDE, N and size class
  * (floor(log2 cells)); with the environment variable DG_AUTOTUNE_FILE set, choices are also
  * appended to that file and read back by later processes.  Synchronises the stream.
- * stage_ty (0 in 1D) and limit_blocks_per_sm are optional outputs.  Errors: DG_EINVAL,
+ * stage_ty (0 in 1D), limit_blocks_per_sm and persistent are optional outputs.  Errors: DG_EINVAL,
  * DG_ESTATE (a step left unfinished). */
-dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm);
+dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm, int* persistent);
 
 /* Number of kernels the library launched since the mesh was created (graph replays count
  * every kernel node they contain). */

@@ -79,7 +79,8 @@ def lib():
             l.dg_flag_statistics.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
             l.dg_flag_statistics.restype = ctypes.c_int
-            l.dg_autotune.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            l.dg_autotune.argtypes = [P, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
             l.dg_autotune.restype = ctypes.c_int
             l.dg_indicator_logits.argtypes = [P, P]
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
@@ -227,10 +228,11 @@ class Mesh:
         _check(lib().dg_set_indicator_mlp(self._h, net._h, tau))
 
     def autotune(self, dt):
-        """Chooses the stage tile height and the limiter grid on this mesh (see dg_autotune)."""
-        a, b = ctypes.c_int(0), ctypes.c_int(0)
-        _check(lib().dg_autotune(self._h, dt, ctypes.byref(a), ctypes.byref(b)))
-        return int(a.value), int(b.value)
+        """Chooses the stage tile height and launch form and the limiter grid on this mesh
+        (see dg_autotune); returns (tile rows, limiter blocks per SM, persistent)."""
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().dg_autotune(self._h, dt, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
 
     def flag_statistics(self, reset=False):
         """(TVB-flagged, limited, passes) totals over the dg_step limiter passes."""

@@ -30,7 +30,7 @@ void launch_scatter1(int pde, int N, const LaunchArgs& a, const double* lim, con
                      int nblocks);
 void launch_project1(int pde, int N, const LaunchArgs& a, const int* cell_inst, int kind, const double* params, int np);
 void launch_speed1(int pde, int N, const LaunchArgs& a, const int* cell_inst, double* out);
-void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys);
+void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys, int* queue, int grid);
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc, int* li);
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt, double* lim,
                    int nblocks);
@@ -146,6 +146,8 @@ struct dg_mesh {
   int stage_ty = 8;
   Tile* d_stage_tiles = nullptr;
   int n_stage_tiles = 0;
+  int stage_persistent = 0;  // persistent tile queue (1) or one block per tile (0)
+  int* d_queue = nullptr;
   long long launches = 0;
   // CUDA graph of one full step
   cudaGraphExec_t gexec = nullptr;
@@ -180,6 +182,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_inst);
   cudaFree(m->d_tiles);
   cudaFree(m->d_stage_tiles);
+  cudaFree(m->d_queue);
   cudaFree(m->d_cell_inst);
   for (auto& p : m->U) cudaFree(p);
   cudaFree(m->lim);
@@ -199,13 +202,13 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
 // ----------------------------------------------------------------------------- autotuning
 // Process-wide choices per (dim, pde, N, mesh-size class = floor(log2 cells)); optionally
 // loaded from and appended to the text file named by DG_AUTOTUNE_FILE
-// ("dim pde N class stage_ty limit_blocks_per_sm" per line).
+// ("dim pde N class stage_ty limit_blocks_per_sm persistent" per line).
 struct TuneKey {
   int dim, pde, N, cls;
   bool operator==(const TuneKey& o) const { return dim == o.dim && pde == o.pde && N == o.N && cls == o.cls; }
 };
 struct TuneVal {
-  int stage_ty, limit_per_sm;
+  int stage_ty, limit_per_sm, persistent;
 };
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
 static bool g_tune_loaded = false;
@@ -225,8 +228,11 @@ static void tune_load() {
   if (!fp) return;
   TuneKey k;
   TuneVal v;
-  while (fscanf(fp, "%d %d %d %d %d %d", &k.dim, &k.pde, &k.N, &k.cls, &v.stage_ty, &v.limit_per_sm) == 6)
-    if ((v.stage_ty == 4 || v.stage_ty == 8) && v.limit_per_sm >= 1 && v.limit_per_sm <= 64) g_tune.push_back({k, v});
+  while (fscanf(fp, "%d %d %d %d %d %d %d", &k.dim, &k.pde, &k.N, &k.cls, &v.stage_ty, &v.limit_per_sm,
+                &v.persistent) == 7)
+    if ((v.stage_ty == 4 || v.stage_ty == 8) && v.limit_per_sm >= 1 && v.limit_per_sm <= 64 &&
+        (v.persistent == 0 || v.persistent == 1))
+      g_tune.push_back({k, v});
   fclose(fp);
 }
 
@@ -342,8 +348,10 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   tune_load();
   const TuneVal* tv = tune_find(TuneKey{dim, pde, N, size_class(off)});
   if (tv) m->limit_blocks = m->sms * tv->limit_per_sm;
+  if (tv) m->stage_persistent = tv->persistent;
   if (dim == 2) {
     e = prepare2(pde, N);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_queue, sizeof(int));
     if (e == cudaSuccess) e = build_stage_tiles(m, tv ? tv->stage_ty : 8);
     if (e != cudaSuccess) {
       dg_mesh_destroy(m);
@@ -380,7 +388,8 @@ static void k_stage(dg_mesh* m, int stage, int in, int out, double dt_all) {
     LaunchArgs a = args<LaunchArgs>(m, 0, in, out);
     a.tiles = m->d_stage_tiles;
     a.ntiles = m->n_stage_tiles;
-    launch_stage2(m->pde, m->N, a, stage, dt_all, m->stage_ty);
+    if (m->stage_persistent) cudaMemsetAsync(m->d_queue, 0, sizeof(int), m->st);
+    launch_stage2(m->pde, m->N, a, stage, dt_all, m->stage_ty, m->stage_persistent ? m->d_queue : nullptr, m->sms);
   }
   m->launches++;
 }
@@ -713,10 +722,11 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
 }
 
 // Times the candidate configurations on this mesh's current state (u^n is left unchanged):
-// the 2D stage tile height (4 or 8 rows) on stage 1, then the limiter's grid (2, 4, 8 or 16
-// blocks per SM) on the TVB-flagged cells of that stage.  The fastest are applied to the
+// the 2D stage tile height (4 or 8 rows) and launch form (one block per tile, or a
+// persistent grid taking tiles from a queue) on stage 1, then the limiter's grid (2, 4, 8
+// or 16 blocks per SM) on the TVB-flagged cells of that stage.  The fastest are applied to the
 // mesh and remembered for meshes of the same kind and size class.
-extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm) {
+extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm, int* persistent) {
   if (!m || !(dt > 0.0)) return fail(DG_EINVAL, "bad arguments");
   if (m->last_stage != 0 && m->last_stage != 3) return fail(DG_ESTATE, "a step was left unfinished");
   cudaEvent_t e0, e1;
@@ -737,16 +747,20 @@ extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limi
     return best;
   };
   m->cur = 0;
-  int best_ty = m->stage_ty;
+  int best_ty = m->stage_ty, best_pers = m->stage_persistent;
   if (m->dim == 2) {
     float best = 1e30f;
     for (int ty : {8, 4}) {
       cudaError_t e = build_stage_tiles(m, ty);
       if (e != cudaSuccess) return fail(DG_ECUDA, "stage tiles: %s", cudaGetErrorString(e));
-      const float ms = time_it([&] { k_stage(m, 1, 0, 1, dt); }, 3);
-      if (ms < best) { best = ms; best_ty = ty; }
+      for (int pers : {0, 1}) {
+        m->stage_persistent = pers;
+        const float ms = time_it([&] { k_stage(m, 1, 0, 1, dt); }, 3);
+        if (ms < best) { best = ms; best_ty = ty; best_pers = pers; }
+      }
     }
     CK(build_stage_tiles(m, best_ty));
+    m->stage_persistent = best_pers;
   }
   // limiter grid on the flagged cells of stage 1 (writes only the limiter scratch)
   k_stage(m, 1, 0, 1, dt);
@@ -777,15 +791,16 @@ extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limi
     m->gexec = nullptr;
   }
   const TuneKey k{m->dim, m->pde, m->N, size_class(m->ncell)};
-  g_tune.push_back({k, TuneVal{best_ty, best_mult}});
+  g_tune.push_back({k, TuneVal{best_ty, best_mult, best_pers}});
   if (const char* f = getenv("DG_AUTOTUNE_FILE")) {
     if (FILE* fp = fopen(f, "a")) {
-      fprintf(fp, "%d %d %d %d %d %d\n", k.dim, k.pde, k.N, k.cls, best_ty, best_mult);
+      fprintf(fp, "%d %d %d %d %d %d %d\n", k.dim, k.pde, k.N, k.cls, best_ty, best_mult, best_pers);
       fclose(fp);
     }
   }
   if (stage_ty) *stage_ty = m->dim == 2 ? best_ty : 0;
   if (limit_blocks_per_sm) *limit_blocks_per_sm = best_mult;
+  if (persistent) *persistent = m->dim == 2 ? best_pers : 0;
   return DG_OK;
 }
 

@@ -260,7 +260,7 @@ template <int PDE, int N, int TYS>
 __global__ void __launch_bounds__((TYS + 3) * 32, 1)
     k_stage2(const double* __restrict__ un, const double* __restrict__ us, double* __restrict__ out,
              const Inst* __restrict__ insts, const Tile* __restrict__ tiles, long long ctot, int bc, int stage,
-             double dt_all, double gam) {
+             double dt_all, double gam, int ntiles, int* __restrict__ queue) {
   using O = Off<N>;
   constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1, QV = Q * V;
   // east traces, then x-face fluxes: [QV][TYS][TX+1]; north traces, then y-face fluxes:
@@ -270,7 +270,16 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
   double* const sNb = smem + QV * TYS * (TX + 1);
 #define sE(qv, r, c) sEb[((qv) * TYS + (r)) * (TX + 1) + (c)]
 #define sN(qv, r, c) sNb[((qv) * (TYS + 1) + (r)) * TX + (c)]
-  const Tile tile = tiles[blockIdx.x];
+  // one tile per block, or (queue != null) a persistent block taking tiles from the queue
+  __shared__ int s_tile;
+  int tix = blockIdx.x;
+  if (queue) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+    __syncthreads();
+    tix = s_tile;
+  }
+  while (tix < ntiles) {
+  const Tile tile = tiles[tix];
   const Inst I = insts[tile.inst];
   const int ncols = min(TX, I.nx - tile.x0), nrows = min(TYS, I.ny - tile.y0);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
   }
   __syncthreads();
   // ---------------------------------------------------------------- phase 3: lift + RK
-  if (!interior) return;
+  if (interior) {
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     // x faces: acc_ab -= psi_a(1) sum_q w_q psi_b(s_q) [F_E(q) - (-1)^a F_W(q)]
@@ -475,6 +484,13 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
       else r = fma(1.0 / 3.0, un[idx], (2.0 / 3.0) * e);
       out[idx] = r;
     }
+  }  // interior
+  if (!queue) break;
+  __syncthreads();  // shared memory and s_tile are reused by the next tile
+  if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1);
+  __syncthreads();
+  tix = s_tile;
+  }  // tiles
 }
 
 #undef sE
@@ -1071,17 +1087,19 @@ cudaError_t prepare2(int pde, int N) {
 }
 
 template <int PDE, int N, int TYS>
-static void run_stage2(const LaunchArgs& a, int stage, double dt_all) {
+static void run_stage2(const LaunchArgs& a, int stage, double dt_all, int* queue, int grid) {
   const size_t bytes = stage_smem2<PDE, N, TYS>();
-  k2::k_stage2<PDE, N, TYS><<<a.ntiles, (TYS + 3) * 32, bytes, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
-                                                                        a.bc, stage, dt_all, a.gam);
+  k2::k_stage2<PDE, N, TYS><<<queue ? grid : a.ntiles, (TYS + 3) * 32, bytes, a.st>>>(
+      a.un, a.us, a.out, a.inst, a.tiles, a.ctot, a.bc, stage, dt_all, a.gam, a.ntiles, queue);
 }
 int tile_w2() { return k2::TX; }
 int tile_h2() { return k2::TY; }
 
-void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys) {
-  if (tys == 4) DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 4>(a, stage, dt_all)));
-  else DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 8>(a, stage, dt_all)));
+// queue != null: persistent launch of `grid` blocks popping tiles from *queue (zeroed by the
+// caller before the launch); otherwise one block per tile
+void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys, int* queue, int grid) {
+  if (tys == 4) DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 4>(a, stage, dt_all, queue, grid)));
+  else DG_DISPATCH2(pde, N, (run_stage2<P_, N_, 8>(a, stage, dt_all, queue, grid)));
 }
 
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc,

@@ -26,20 +26,21 @@ def test_autotune_choices_and_state():
     g.rk_stage(1, dt)
     before = g.get_modes()
     g.set_modes(u0)
-    ty, mult = g.autotune(dt)
-    assert ty in (4, 8) and mult in (2, 4, 8, 16)
+    ty, mult, pers = g.autotune(dt)
+    assert ty in (4, 8) and mult in (2, 4, 8, 16) and pers in (0, 1)
     assert np.array_equal(g.get_modes(), u0)  # u^n untouched
     g.rk_stage(1, dt)
     assert np.array_equal(g.get_modes(), before)  # every face flux computed once either way
 
 
 def test_four_row_tiles_match_oracle_in_fresh_process(tmp_path):
-    """Force the 4-row stage tiles through the tuning file and check a stage, the flags and
-    the limiter against the oracle on a ragged 2D Euler P2 mesh."""
+    """Force the 4-row stage tiles and the persistent tile queue through the tuning file
+    and check a stage, the flags and the limiter against the oracle on a ragged 2D Euler P2
+    mesh."""
     f = tmp_path / "tune.txt"
     nx, ny = 70, 45
     cls = int(np.floor(np.log2(nx * ny)))
-    f.write_text("2 1 2 %d 4 2\n" % cls)
+    f.write_text("2 1 2 %d 4 2 1\n" % cls)  # 4-row tiles, persistent tile queue
     code = textwrap.dedent("""
         import sys, numpy as np
         sys.path.insert(0, %r)
