@@ -388,14 +388,16 @@ static double max_speed(int dim, int pde, double gam, int dir, const double* u) 
 }
 
 /* Local Lax-Friedrichs flux (Sec. 2 names Lax-Friedrichs; local alpha is our reading):
- * f* = 1/2 (f(uL) + f(uR)) - 1/2 alpha (uR - uL), alpha = max(rho(f'(uL)), rho(f'(uR))). */
+ * f* = 1/2 (f(uL) + f(uR)) - 1/2 alpha (uR - uL), alpha = max(rho(f'(uL)), rho(f'(uR))).
+ * Where either spectral radius is undefined (no real sound speed: negative density or
+ * pressure at the face) alpha is NaN, whichever side it comes from. */
 static void llf(int dim, int pde, double gam, int dir, const double* uL, const double* uR, double* fs) {
   int nv = or_nvars(dim, pde);
   double fL[OR_MAXV], fR[OR_MAXV];
   phys_flux(dim, pde, gam, dir, uL, fL);
   phys_flux(dim, pde, gam, dir, uR, fR);
   double aL = max_speed(dim, pde, gam, dir, uL), aR = max_speed(dim, pde, gam, dir, uR);
-  double a = aL > aR ? aL : aR;
+  double a = (isnan(aL) || isnan(aR)) ? NAN : (aL > aR ? aL : aR);
   for (int v = 0; v < nv; ++v) fs[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * a * (uR[v] - uL[v]);
 }
 

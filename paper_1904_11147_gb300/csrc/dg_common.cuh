@@ -122,7 +122,12 @@ __device__ __forceinline__ void llf(int dir, const double* uL, const double* uR,
   double fL[V], fR[V], aL, aR;
   Phys<DIM, PDE>::flux(dir, uL, fL, aL, gam, gm1);
   Phys<DIM, PDE>::flux(dir, uR, fR, aR, gam, gm1);
-  double a = fmax(aL, aR);
+  // fmax drops a NaN operand; a face state without a real sound speed (negative density
+  // or pressure at a quadrature point) must instead make alpha, and the step, non-finite.
+  // The NaN test runs on the bit patterns (integer pipe).
+  constexpr unsigned long long kAbs = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+  const bool nan_lr = ((__double_as_longlong(aL) & kAbs) > kInf) | ((__double_as_longlong(aR) & kAbs) > kInf);
+  const double a = nan_lr ? aL + aR : fmax(aL, aR);
 #pragma unroll
   for (int v = 0; v < V; ++v) fs[v] = inv_h * fma(-a, uR[v] - uL[v], fL[v] + fR[v]);
 }
