@@ -175,12 +175,20 @@ def dist_init():
 
 
 def max_over_ranks(dist, x):
+    """Largest value over the ranks (the job's time is the slowest rank's)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank, steps, ms_max, world):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest
+    rank's time."""
+    return units_per_rank * steps * world / (ms_max / 1e3)
 
 
 def barrier(dist):
@@ -322,8 +330,8 @@ def main():
         else:
             ms_plain, launches, clk_plain, tvb_frac, lim_plain = timed_arm(mesh, dgl.IND_TVB, args.clocks_out)
             lmesh, ind_main, ms, clk, lim_learned, fallbacks, failures = mesh, dgl.IND_TVB, ms_plain, clk_plain, lim_plain, 0, 0
-        value = dofs * args.steps * world / (ms / 1e3)
-        value_plain = dofs * args.steps * world / (ms_plain / 1e3)
+        value = aggregate_rate(dofs, args.steps, ms, world)
+        value_plain = aggregate_rate(dofs, args.steps, ms_plain, world)
 
         # ------------------------------------------------------------ dominant kernel alone
         mesh.set_modes(u0)

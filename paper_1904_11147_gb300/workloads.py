@@ -118,9 +118,11 @@ def burgers_2d_batched(n_inst: int = 64, N: int = 2, lo: int = 64, hi: int = 512
 
 
 def euler_2d_batched(n_inst: int = 256, N: int = 3, lo: int = 128, hi: int = 1024, seed: int = SEED) -> Workload:
-    """Batched 2D Euler four-quadrant problems, sides log-uniform in [lo, hi]."""
+    """Batched 2D Euler four-quadrant problems, sides log-uniform in [lo, hi] rounded to even
+    numbers, so that the quadrant lines x = y = 0.5 fall on cell faces (a jump inside a cell
+    makes the projected P3 polynomial lose positivity at quadrature points)."""
     rng = np.random.default_rng(seed)
-    sides = [int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(n_inst)]
+    sides = [2 * int(round(0.5 * math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(n_inst)]
     params = [quadrant_states(rng) for _ in range(n_inst)]
     return Workload("euler2d_batched_p%d_x%d" % (N, n_inst), 2, PDE_EULER, N, sides, sides,
                     [(0.0, 1.0, 0.0, 1.0)] * n_inst, BC_OUTFLOW, IC_QUADRANT, params, 0.25)

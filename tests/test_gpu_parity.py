@@ -237,6 +237,45 @@ def test_batched_instances_parity():
         off += nx * ny
 
 
+def test_batched_euler_p3_instances_parity():
+    """Three 2D Euler P3 four-quadrant instances of uneven sizes (one not square) with their
+    own states and time steps in one mesh, 20 steps; each instance matches the oracle run
+    on its own (per-step shadow: the oracle steps from the GPU's previous state)."""
+    import torch
+    st = torch.cuda.Stream()
+    sizes = [(24, 24), (38, 38), (20, 30)]
+    box = (0.0, 1.0, 0.0, 1.0)
+    params = [W.euler_2d_quadrant(8, 3, seed=s).params[0] for s in (1907, 31, 77)]
+    g = dgl.Mesh(2, 1, 3, [s[0] for s in sizes], [s[1] for s in sizes], [box] * 3, bc=1, stream=st.cuda_stream)
+    g.project_ic(W.IC_QUADRANT, params)
+    os_, dts, off = [], [], 0
+    u0 = g.get_modes()
+    for (nx, ny), p in zip(sizes, params):
+        o = oracle.Mesh(2, 1, 3, nx, ny, box=box, bc=1)
+        assert _rel(u0[off:off + nx * ny], o.project_ic(W.IC_QUADRANT, p)) < 1e-13
+        ws = o.max_wavespeed(u0[off:off + nx * ny])
+        dts.append(0.1 / (ws[0] * nx + ws[1] * ny))
+        os_.append(o)
+        off += nx * ny
+    g.set_dt(dts)
+    worst = 0.0
+    with torch.cuda.stream(st):
+        for k in range(20):
+            prev = g.get_modes()
+            g.step(0.0)
+            got = g.get_modes()
+            off = 0
+            for (nx, ny), o, dt in zip(sizes, os_, dts):
+                ref, _, near = o.step(prev[off:off + nx * ny], dt)
+                d = _rel(got[off:off + nx * ny], ref)
+                assert np.isfinite(ref).all()
+                if not near:
+                    assert d <= 1e-11, (k, d)
+                    worst = max(worst, d)
+                off += nx * ny
+    print("batched Euler P3: worst per-step deviation %.2e" % worst)
+
+
 def test_full_size_sampled_parity():
     """The 1024 x 1024 2D Euler P2 four-quadrant workload in the launch configuration the
     benchmark uses: one stage + indicator + limiter on the GPU; the oracle recomputes
