@@ -69,6 +69,11 @@ def lib():
             l.or_csweno_limit.argtypes = [M, _D, _U8, _D, ctypes.c_double]
             l.or_step.argtypes = [M, ctypes.c_double, _D, ctypes.c_double, ctypes.c_int, ctypes.c_double, _L]
             l.or_step.restype = ctypes.c_long
+            l.or_step_pp.argtypes = [M, ctypes.c_double, _D, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_double, _L, _L, _L]
+            l.or_step_pp.restype = ctypes.c_long
+            l.or_positivity_limit.argtypes = [M, _D, ctypes.c_double, _L]
+            l.or_positivity_limit.restype = ctypes.c_long
             l.or_max_wavespeed.argtypes = [M, _D, _D]
             l.or_project_ic.argtypes = [M, ctypes.c_int, _D, _D]
             l.or_euler_eigen.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D, _D]
@@ -164,6 +169,25 @@ class Mesh:
         near = ctypes.c_long(0)
         nf = lib().or_step(self._ref(), dt, _dp(u), M, int(limit), eps, ctypes.byref(near))
         return u, int(nf), int(near.value)
+
+    def positivity_limit(self, u, eps0=1e-13):
+        """Zhang-Shu positivity-preserving scaling (Euler). Returns (u_new, cells changed,
+        cells with an inadmissible mean)."""
+        u = self._chk(u).copy()
+        bad = ctypes.c_long(0)
+        n = lib().or_positivity_limit(self._ref(), _dp(u), eps0, ctypes.byref(bad))
+        if n < 0:
+            raise ValueError("the positivity-preserving scaling is defined for the Euler equations")
+        return u, int(n), int(bad.value)
+
+    def step_pp(self, u, dt, M=0.01, limit=True, eps=1e-6, pp=True, pp_eps=1e-13):
+        """SSP-RK3 step with the positivity-preserving scaling after each stage's limiter.
+        Returns (u_new, n_flagged, n_near, n_changed, n_bad)."""
+        u = self._chk(u).copy()
+        near, npp, bad = ctypes.c_long(0), ctypes.c_long(0), ctypes.c_long(0)
+        nf = lib().or_step_pp(self._ref(), dt, _dp(u), M, int(limit), eps, int(pp), pp_eps, ctypes.byref(near),
+                              ctypes.byref(npp), ctypes.byref(bad))
+        return u, int(nf), int(near.value), int(npp.value), int(bad.value)
 
     def max_wavespeed(self, u):
         u = self._chk(u)

@@ -1000,6 +1000,176 @@ long or_step(const or_mesh* m, double dt, double* u, double M, int limit, double
 }
 
 /* ------------------------------------------------------------------------------------
+ * Positivity-preserving scaling (Example 11 adds it to the limiter, following Zhang and
+ * Shu, ref. [zs3]), Euler only.  For each cell with mean state Ubar (rho > 0, p > 0):
+ *   eps = min(eps0, rhobar, pbar);
+ *   S   = the check points: in 1D the L-point Gauss-Lobatto rule with 2L-3 >= N
+ *         (L = 2 for N = 1, else 3); in 2D the union of (Gauss x Gauss-Lobatto) and
+ *         (Gauss-Lobatto x Gauss) with the (N+1)-point Gauss rule of the face integrals;
+ *   1) rho_min = min_S rho_h; if rho_min < eps the density's modes n >= 1 are scaled
+ *      by theta1 = (rhobar - eps) / (rhobar - rho_min);
+ *   2) for every q in S with p(U_q) < eps (U_q the point value after step 1), t_q in
+ *      [0,1] solves p((1-t) Ubar + t U_q) = eps; theta2 = min_q t_q (1 when no point
+ *      is below eps) scales the modes n >= 1 of every variable.
+ * Multiplying p by the positive density turns the equation of step 2 into the quadratic
+ *   A t^2 + B t + C = 0,  D = U_q - Ubar,
+ *   A = (g-1) (D_E D_rho - |D_m|^2 / 2),
+ *   B = (g-1) (Ebar D_rho + rhobar D_E - mbar . D_m) - eps D_rho,
+ *   C = (g-1) (Ebar rhobar - |mbar|^2 / 2) - eps rhobar  (= rhobar (pbar - eps) >= 0),
+ * which changes sign on [0,1] (C >= 0 > value at t = 1); its root there is taken from the
+ * cancellation-free pair q = -(B + sign(B) sqrt(B^2 - 4AC)) / 2, roots q/A and C/q, and
+ * moved 1e-12 (relative) towards 0: near vacuum p changes by ~1e5 per unit of t, so a
+ * root rounded by one ulp could leave p below zero, while the shift raises p by far
+ * more than that rounding (p is concave along the segment, so every t below the root
+ * is admissible).
+ * Cells whose mean is not admissible are left alone and counted in *n_bad.  Returns the
+ * number of cells changed.
+ * ----------------------------------------------------------------------------------*/
+static double pp_pressure(int dim, double gam, const double* q) {
+  const int nv = dim == 1 ? 3 : 4;
+  double k = q[1] * q[1];
+  if (dim == 2) k += q[2] * q[2];
+  return (gam - 1.0) * (q[nv - 1] - 0.5 * k / q[0]);
+}
+
+static double pp_root(int dim, double gam, double eps, const double* ub, const double* uq) {
+  const int nv = dim == 1 ? 3 : 4;
+  const double g1 = gam - 1.0;
+  double D[OR_MAXV];
+  for (int v = 0; v < nv; ++v) D[v] = uq[v] - ub[v];
+  double dm2 = D[1] * D[1], mdm = ub[1] * D[1], m2 = ub[1] * ub[1];
+  if (dim == 2) { dm2 += D[2] * D[2]; mdm += ub[2] * D[2]; m2 += ub[2] * ub[2]; }
+  const double A = g1 * (D[nv - 1] * D[0] - 0.5 * dm2);
+  const double B = g1 * (ub[nv - 1] * D[0] + ub[0] * D[nv - 1] - mdm) - eps * D[0];
+  const double C = g1 * (ub[nv - 1] * ub[0] - 0.5 * m2) - eps * ub[0];
+  double t;
+  if (A == 0.0) {
+    t = -C / B;
+  } else {
+    const double disc = B * B - 4.0 * A * C;
+    const double sq = sqrt(disc > 0.0 ? disc : 0.0);
+    const double q = -0.5 * (B + (B >= 0.0 ? sq : -sq));
+    const double r1 = q / A, r2 = C / q;
+    t = (r2 >= 0.0 && r2 <= 1.0) ? r2 : r1;
+  }
+  t *= 1.0 - 1e-12;
+  return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+}
+
+long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) {
+  if (m->pde != 1) return -1;
+  const int dim = m->dim, N = m->N, nv = or_nvars(dim, 1), np = or_nmodes(dim, N);
+  const int L = N == 1 ? 2 : 3;
+  const ld glx[3] = {-1.0L, 0.0L, 1.0L}, glx2[2] = {-1.0L, 1.0L};
+  const ld* gl = L == 2 ? glx2 : glx;
+  ld gx[OR_MAXQ], gw[OR_MAXQ];
+  gauss_rule(N + 1, gx, gw);
+  /* check points (r, s) and the basis values there */
+  int npt = 0;
+  double phi[2 * OR_MAXQ * 3][OR_MAXNP];
+  if (dim == 1) {
+    for (int i = 0; i < L; ++i, ++npt)
+      for (int k = 0; k < np; ++k) phi[npt][k] = (double)psi(k, gl[i]);
+  } else {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i <= N; ++i)
+        for (int j = 0; j < L; ++j, ++npt) {
+          const ld r = pass == 0 ? gx[i] : gl[j], t = pass == 0 ? gl[j] : gx[i];
+          for (int k = 0; k < np; ++k) {
+            int a, b;
+            mode_ab(k, &a, &b);
+            phi[npt][k] = (double)(psi(a, r) * psi(b, t));
+          }
+        }
+  }
+  const double c0 = dim == 1 ? (double)psi(0, 0) : (double)(psi(0, 0) * psi(0, 0));
+  long changed = 0, bad = 0;
+  for (size_t c = 0; c < (size_t)m->nx * m->ny; ++c) {
+    double* uc = u + c * nv * np;
+    double ub[OR_MAXV];
+    for (int v = 0; v < nv; ++v) ub[v] = uc[v * np] * c0;
+    const double pb = pp_pressure(dim, m->gamma, ub);
+    if (!(ub[0] > 0.0) || !(pb > 0.0)) { ++bad; continue; }
+    double eps = eps0;
+    if (ub[0] < eps) eps = ub[0];
+    if (pb < eps) eps = pb;
+    int touched = 0;
+    /* 1) density */
+    double rmin = ub[0];
+    for (int q = 0; q < npt; ++q) {
+      double r = 0.0;
+      for (int k = 0; k < np; ++k) r += uc[k] * phi[q][k];
+      if (r < rmin) rmin = r;
+    }
+    if (rmin < eps) {
+      const double th1 = (ub[0] - eps) / (ub[0] - rmin);
+      for (int k = 1; k < np; ++k) uc[k] *= th1;
+      touched = 1;
+    }
+    /* 2) pressure */
+    double th2 = 1.0;
+    for (int q = 0; q < npt; ++q) {
+      double uq[OR_MAXV];
+      for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int k = 0; k < np; ++k) s += uc[v * np + k] * phi[q][k];
+        uq[v] = s;
+      }
+      if (pp_pressure(dim, m->gamma, uq) < eps) {
+        const double t = pp_root(dim, m->gamma, eps, ub, uq);
+        if (t < th2) th2 = t;
+      }
+    }
+    if (th2 < 1.0) {
+      for (int v = 0; v < nv; ++v)
+        for (int k = 1; k < np; ++k) uc[v * np + k] *= th2;
+      touched = 1;
+    }
+    changed += touched;
+  }
+  if (n_bad) *n_bad = bad;
+  return changed;
+}
+
+/* One SSP-RK3 step as or_step, with the positivity-preserving scaling after the limiter
+ * of every stage when pp is set (Euler).  *n_pp (if given) receives the number of cell
+ * changes over the three stages and *n_bad the cells whose mean was not admissible. */
+long or_step_pp(const or_mesh* m, double dt, double* u, double M, int limit, double eps, int pp, double pp_eps,
+                long* n_near, long* n_pp, long* n_bad) {
+  size_t ncell = (size_t)m->nx * m->ny;
+  size_t n = ncell * or_nvars(m->dim, m->pde) * or_nmodes(m->dim, m->N);
+  double* un = (double*)malloc(n * sizeof(double));
+  double* keep = (double*)malloc(n * sizeof(double));
+  double* a = (double*)malloc(n * sizeof(double));
+  double* b = (double*)malloc(n * sizeof(double));
+  unsigned char* fl = (unsigned char*)malloc(ncell);
+  long nf = 0, nn = 0, near = 0, np_ = 0, nb = 0, bad = 0;
+  memcpy(un, u, n * sizeof(double));
+  const double* prev = un;
+  for (int s = 1; s <= 3; ++s) {
+    or_rk_stage(m, s, dt, un, prev, a);
+    if (limit) {
+      nf += or_flag_tvb(m, a, M, fl, &near);
+      nn += near;
+      or_csweno_limit(m, a, fl, b, eps);
+      double* t = a; a = b; b = t;
+    }
+    if (pp) {
+      np_ += or_positivity_limit(m, a, pp_eps, &bad);
+      nb += bad;
+    }
+    memcpy(keep, a, n * sizeof(double));
+    prev = keep;
+  }
+  memcpy(u, a, n * sizeof(double));
+  if (n_near) *n_near = nn;
+  if (n_pp) *n_pp = np_;
+  if (n_bad) *n_bad = nb;
+  free(un); free(keep); free(a); free(b); free(fl);
+  return nf;
+}
+
+/* ------------------------------------------------------------------------------------
  * Largest characteristic speed over the cell means (for the CFL time step), per
  * direction: out[0] = x, out[1] = y (2D only).
  * ----------------------------------------------------------------------------------*/
