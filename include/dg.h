@@ -121,6 +121,28 @@ dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flag
  * reads the unlimited neighbours.  Errors: DG_ESTATE if no flags exist for this state. */
 dg_status dg_cswenolimit(dg_mesh* m);
 
+/* Positivity-preserving scaling (Example 11 adds it to the limiter, following Zhang and
+ * Shu, ref. [zs3]) of the current state, every cell, Euler only.  For a cell whose mean
+ * Ubar has rho > 0 and p > 0, with eps = min(eps0, rhobar, pbar): the density's modes
+ * n >= 1 are scaled so that rho >= eps at the check points, then every variable's modes
+ * n >= 1 by the largest theta in [0,1] that keeps p >= eps there (the root of a quadratic
+ * in theta per point, taken 1e-12 relative below it).  Check points: the Gauss-Lobatto
+ * points -1, 0, 1 (-1, 1 for N = 1) in 1D; in 2D (Gauss x Gauss-Lobatto) and
+ * (Gauss-Lobatto x Gauss) with the N+1 face Gauss points.  Means are left bitwise; cells
+ * with an inadmissible mean are left alone and counted (dg_positivity_counts).
+ * Asynchronous.  Errors: DG_EINVAL (Burgers, eps0 not positive and finite). */
+dg_status dg_positivity_limit(dg_mesh* m, double eps0);
+
+/* enable != 0: dg_step applies dg_positivity_limit(eps0) after the limiter of every
+ * stage (the CUDA graph is rebuilt on the next dg_step); 0 switches it off (default).
+ * Errors: DG_EINVAL (Burgers, eps0 not positive and finite when enabling). */
+dg_status dg_set_positivity(dg_mesh* m, int enable, double eps0);
+
+/* Running totals of the scaling since mesh creation or the last reset: cells changed and
+ * cells whose mean was not admissible (left alone).  Returns DG_EPOSITIVITY when
+ * bad_means > 0.  Synchronises the stream. */
+dg_status dg_positivity_counts(dg_mesh* m, int64_t* changed, int64_t* bad_means, int reset);
+
 /* One full SSP-RK3 step: three times (stage, indicator, limiter), replayed from a CUDA
  * graph captured on the first call.  dt as in dg_rk_stage. */
 dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M);

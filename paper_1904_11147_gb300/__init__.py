@@ -84,11 +84,16 @@ def lib():
             l.dg_autotune.restype = ctypes.c_int
             l.dg_indicator_logits.argtypes = [P, P]
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
+            l.dg_positivity_limit.argtypes = [P, ctypes.c_double]
+            l.dg_set_positivity.argtypes = [P, ctypes.c_int, ctypes.c_double]
+            l.dg_positivity_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.c_int]
             for name in ("dg_mesh_create", "dg_mesh_destroy", "dg_set_modes", "dg_get_modes", "dg_project_ic",
                          "dg_set_dt", "dg_rk_stage", "dg_flag_cells", "dg_cswenolimit", "dg_step",
                          "dg_max_wavespeed", "dg_limiter_tables", "dg_mlp_create", "dg_mlp_destroy",
                          "dg_mlp_get_params", "dg_mlp_set_params", "dg_mlp_grad", "dg_mlp_train_step",
-                         "dg_set_indicator_mlp", "dg_indicator_logits", "dg_harvest", "dg_mlp_predict"):
+                         "dg_set_indicator_mlp", "dg_indicator_logits", "dg_harvest", "dg_mlp_predict",
+                         "dg_positivity_limit", "dg_set_positivity", "dg_positivity_counts"):
                 getattr(l, name).restype = ctypes.c_int
             _lib = l
     return _lib
@@ -207,6 +212,20 @@ class Mesh:
 
     def step(self, dt, indicator=IND_TVB, M=0.01):
         _check(lib().dg_step(self._h, dt, indicator, M))
+
+    def positivity_limit(self, eps0=1e-13):
+        """Positivity-preserving scaling of the current state (see dg_positivity_limit)."""
+        _check(lib().dg_positivity_limit(self._h, eps0))
+
+    def set_positivity(self, enable=True, eps0=1e-13):
+        """Apply the positivity-preserving scaling after every stage's limiter in step()."""
+        _check(lib().dg_set_positivity(self._h, int(enable), eps0))
+
+    def positivity_counts(self, reset=False):
+        """(cells changed, cells with an inadmissible mean) by the scaling so far."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        lib().dg_positivity_counts(self._h, ctypes.byref(a), ctypes.byref(b), int(reset))
+        return int(a.value), int(b.value)
 
     def max_wavespeed(self):
         out = np.zeros(2 * self.n_inst)

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcswenodg.so")
-SOURCES = ["dg_kernels2d.cu", "dg_kernels1d.cu", "dg_mlp.cu", "dg_api.cu", "dg_noalloc.cu", "tables.cpp"]
+SOURCES = ["dg_kernels2d.cu", "dg_kernels1d.cu", "dg_mlp.cu", "dg_api.cu", "dg_noalloc.cu", "dg_positivity.cu",
+           "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -71,6 +71,9 @@ void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* p
                             double gam, const int* lc, const int* li, const Counters* cnt, const unsigned char* flags,
                             int skip_kept, unsigned int* fail, int nblocks);
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total);
+void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
+                       const double* phi, int npt, double c0, double gam, double eps0,
+                       unsigned long long* counts, int nblocks);
 }  // namespace dg
 
 using namespace dg;
@@ -168,6 +171,15 @@ struct dg_mesh {
   bool use_b = false;                        // dg_cswenolimit limits list B (learned) or A (TVB)
   unsigned long long* flag_totals = nullptr;  // TVB-flagged, limited, passes (dg_step)
   double psi_q[16], psi_p1[4];
+  // positivity-preserving scaling (Euler): basis values at the check points, the
+  // dg_step option and the running counts (cells changed, inadmissible means)
+  std::vector<double> pp_phi;
+  int pp_npt = 0;
+  bool pp_on = false;
+  double pp_eps0 = 1e-13;
+  unsigned long long* pp_counts = nullptr;
+  bool g_pp = false;
+  double g_pp_eps = 0.0;
 };
 
 static size_t mesh_doubles(const dg_mesh* m) { return (size_t)m->ncell * m->V * m->NP; }
@@ -195,6 +207,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->mlp_buf);
   cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
   cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->save); cudaFree(m->fail); cudaFree(m->pos_counts);
+  cudaFree(m->pp_counts);
   delete m;
   return DG_OK;
 }
@@ -325,7 +338,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->flags, m->ctot) && alloc((void**)&m->list_cell, sizeof(int) * m->ctot) &&
             alloc((void**)&m->list_inst, sizeof(int) * m->ctot) && alloc((void**)&m->cnt, sizeof(Counters)) &&
             alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst) &&
-            alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long));
+            alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long)) &&
+            alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long));
   if (!ok) {
     cudaGetLastError();
     dg_mesh_destroy(m);
@@ -337,9 +351,32 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (e == cudaSuccess) e = cudaMemset(m->U[0], 0, plane);
   if (e == cudaSuccess) e = cudaMemset(m->cnt, 0, sizeof(Counters));
   if (e == cudaSuccess) e = cudaMemset(m->flag_totals, 0, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(m->pp_counts, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     dg_mesh_destroy(m);
     return fail(DG_ECUDA, "mesh upload: %s", cudaGetErrorString(e));
+  }
+  if (pde == DG_EULER) {
+    // check points of the positivity-preserving scaling: Gauss-Lobatto points (-1, 0, 1;
+    // -1, 1 for N = 1) in 1D; (Gauss x Gauss-Lobatto) then (Gauss-Lobatto x Gauss) in 2D
+    const dgt::Tabs& tb = g_tabs[N - 1];
+    const int L = N == 1 ? 2 : 3;
+    const double* gl[3] = {tb.psi_m1, N == 1 ? tb.psi_p1 : tb.psi_0, tb.psi_p1};
+    const int NP = m->NP;
+    if (dim == 1) {
+      for (int j = 0; j < L; ++j)
+        for (int k = 0; k < NP; ++k) m->pp_phi.push_back(gl[j][k]);
+      m->pp_npt = L;
+    } else {
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i <= N; ++i)
+          for (int j = 0; j < L; ++j)
+            for (int k = 0; k < NP; ++k) {
+              const int a = mode_a(k), b = mode_b(k);
+              m->pp_phi.push_back(pass == 0 ? tb.psi_q[i][a] * gl[j][b] : gl[j][a] * tb.psi_q[i][b]);
+            }
+      m->pp_npt = 2 * (N + 1) * L;
+    }
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
@@ -474,6 +511,15 @@ static void k_limit_list(dg_mesh* m, const int* lc, const int* li, const Counter
 static void k_limit(dg_mesh* m) {
   if (m->use_b) k_limit_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
   else k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
+}
+
+// positivity-preserving scaling of the current state, every cell (Euler)
+static void k_pp(dg_mesh* m, double eps0) {
+  const long long want = (m->ncell + 127) / 128;
+  const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
+  launch_positivity(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->pp_phi.data(), m->pp_npt,
+                    mean_factor(m), m->gamma, eps0, m->pp_counts, nb);
+  m->launches++;
 }
 
 // Adds the TVB list length and the limited list length of one pass to running totals
@@ -634,6 +680,36 @@ extern "C" dg_status dg_cswenolimit(dg_mesh* m) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_positivity_limit(dg_mesh* m, double eps0) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (m->pde != DG_EULER) return fail(DG_EINVAL, "the positivity-preserving scaling is defined for the Euler equations");
+  if (!(eps0 > 0.0) || !std::isfinite(eps0)) return fail(DG_EINVAL, "eps0 must be positive and finite");
+  k_pp(m, eps0);
+  CK(cudaGetLastError());
+  m->flags_valid = false;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_positivity(dg_mesh* m, int enable, double eps0) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (enable && m->pde != DG_EULER) return fail(DG_EINVAL, "the positivity-preserving scaling is defined for the Euler equations");
+  if (enable && (!(eps0 > 0.0) || !std::isfinite(eps0))) return fail(DG_EINVAL, "eps0 must be positive and finite");
+  m->pp_on = enable != 0;
+  if (m->pp_on) m->pp_eps0 = eps0;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_positivity_counts(dg_mesh* m, int64_t* changed, int64_t* bad_means, int reset) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  unsigned long long c[2];
+  CK(cudaMemcpyAsync(c, m->pp_counts, sizeof(c), cudaMemcpyDeviceToHost, m->st));
+  if (reset) CK(cudaMemsetAsync(m->pp_counts, 0, sizeof(c), m->st));
+  CK(cudaStreamSynchronize(m->st));
+  if (changed) *changed = (int64_t)c[0];
+  if (bad_means) *bad_means = (int64_t)c[1];
+  return c[1] ? DG_EPOSITIVITY : DG_OK;
+}
+
 extern "C" dg_status dg_max_wavespeed(dg_mesh* m, double* out) {
   if (!m || !out) return fail(DG_EINVAL, "null argument");
   CK(cudaMemsetAsync(m->d_speed, 0, sizeof(double) * 2 * m->n_inst, m->st));
@@ -663,6 +739,7 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
       k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt, nullptr, m->flag_totals);
     }
     m->launches++;
+    if (m->pp_on) k_pp(m, m->pp_eps0);
   }
   CK(cudaGetLastError());
   return DG_OK;
@@ -693,7 +770,7 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
     m->flags_valid = false;
     return s;
   }
-  if (!m->gexec || m->g_ind != indicator || m->g_M != tvb_M) {
+  if (!m->gexec || m->g_ind != indicator || m->g_M != tvb_M || m->g_pp != m->pp_on || m->g_pp_eps != m->pp_eps0) {
     if (m->gexec) {
       cudaGraphExecDestroy(m->gexec);
       m->gexec = nullptr;
@@ -712,6 +789,8 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
     m->launches = before;
     m->g_ind = indicator;
     m->g_M = tvb_M;
+    m->g_pp = m->pp_on;
+    m->g_pp_eps = m->pp_eps0;
   }
   CK(cudaGraphLaunch(m->gexec, m->st));
   m->launches += m->g_kernels;

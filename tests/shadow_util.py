@@ -1,0 +1,80 @@
+"""Stage-by-stage shadow comparison of the CUDA path with the oracle (GPU tests only).
+
+Every step of the GPU trajectory is replayed through the per-call entry points, and each
+sub-step is recomputed by the oracle from the GPU's own input to it, so that every
+comparison starts from identical doubles:
+  - the stage output (dg_rk_stage) within 1e-13 (relative, per variable),
+  - the troubled-cell flags (dg_flag_cells) identical: the indicator's decision is taken
+    in the same FP64 operations on both sides, so identical inputs give identical flags,
+  - the limited state (dg_cswenolimit) within 1e-11,
+  - optionally the positivity-preserving scaling (dg_positivity_limit) within 1e-11.
+The CUDA-graph step (dg_step) from the same state must then reproduce the stage-level
+result bitwise: it launches the same kernels in the same order.
+"""
+import numpy as np
+
+import paper_1904_11147_gb300 as dgl
+
+
+def rel(a, b):
+    b = np.asarray(b)
+    scale = np.maximum(np.abs(b).max(axis=(0, 2)), 1e-300)
+    return float((np.abs(np.asarray(a).reshape(b.shape) - b).max(axis=(0, 2)) / scale).max())
+
+
+def shadow_stages(o, g, u0, dt, steps, M=0.01, pp_eps=None, graph_check=True, stop_on_nonfinite=False, t_end=None):
+    """dt: a number or a function of (step, state).  With t_end the last step is cut to
+    end there.  stop_on_nonfinite: a stage output that is not finite on both sides ends
+    the run (it must be non-finite on both).  Returns (worst stage deviation, worst
+    limited deviation, flagged cells in total, steps done, time reached)."""
+    g.set_modes(u0)
+    if pp_eps is not None:
+        g.set_positivity(True, pp_eps)
+    worst_stage = worst_lim = 0.0
+    flagged = 0
+    t = 0.0
+    for k in range(steps):
+        prev = g.get_modes()
+        if t_end is not None and t >= t_end - 1e-14:
+            return worst_stage, worst_lim, flagged, k, t
+        h = dt(k, prev) if callable(dt) else dt
+        if t_end is not None:
+            h = min(h, t_end - t)
+        us = prev
+        for s in (1, 2, 3):
+            g.rk_stage(s, h)
+            got = g.get_modes()
+            ref = o.rk_stage(s, h, prev, us)
+            if stop_on_nonfinite and not (np.isfinite(got).all() and np.isfinite(ref).all()):
+                assert not np.isfinite(got).all() and not np.isfinite(ref).all(), (k, s)
+                return worst_stage, worst_lim, flagged, k, t
+            d = rel(got, ref)
+            assert d <= 1e-13, (k, s, "stage", d)
+            worst_stage = max(worst_stage, d)
+            fl_g, nf, _ = g.flag_cells(dgl.IND_TVB, M, want=True)
+            fl_o, nf_o, _ = o.flag_tvb(got, M)
+            assert nf == nf_o and np.array_equal(fl_g, fl_o), (k, s, "flags", int((fl_g != fl_o).sum()))
+            flagged += nf
+            g.cswenolimit()
+            lim = g.get_modes()
+            d = rel(lim, o.limit(got, fl_o))
+            assert d <= 1e-11, (k, s, "limiter", d)
+            worst_lim = max(worst_lim, d)
+            if pp_eps is not None:
+                g.positivity_limit(pp_eps)
+                scaled = g.get_modes()
+                ref_pp, _, bad = o.positivity_limit(lim, pp_eps)
+                assert bad == 0
+                d = rel(scaled, ref_pp)
+                assert d <= 1e-11, (k, s, "positivity", d)
+                lim = scaled
+            us = lim
+        assert np.isfinite(us).all(), k
+        if graph_check:
+            g.set_modes(prev)
+            g.step(h, dgl.IND_TVB, M)
+            assert np.array_equal(g.get_modes(), us), (k, "graph step differs from the stage calls")
+        else:
+            g.set_modes(us)
+        t += h
+    return worst_stage, worst_lim, flagged, steps, t
