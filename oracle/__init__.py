@@ -73,6 +73,11 @@ def lib():
                                      ctypes.c_int, ctypes.c_double, _L, _L, _L]
             l.or_step_pp.restype = ctypes.c_long
             l.or_positivity_limit.argtypes = [M, _D, ctypes.c_double, _L]
+            l.or_flag_kxrcf.argtypes = [M, _D, _U8, _L, _D]
+            l.or_flag_kxrcf.restype = ctypes.c_long
+            l.or_step_ind.argtypes = [M, ctypes.c_double, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, _L, _L, _L]
+            l.or_step_ind.restype = ctypes.c_long
             l.or_positivity_limit.restype = ctypes.c_long
             l.or_max_wavespeed.argtypes = [M, _D, _D]
             l.or_project_ic.argtypes = [M, ctypes.c_int, _D, _D]
@@ -169,6 +174,26 @@ class Mesh:
         near = ctypes.c_long(0)
         nf = lib().or_step(self._ref(), dt, _dp(u), M, int(limit), eps, ctypes.byref(near))
         return u, int(nf), int(near.value)
+
+    def flag_kxrcf(self, u):
+        """KXRCF troubled-cell flags. Returns (flags, n_flagged, n_near, ratio), ratio the
+        largest indicator value over the indicator variables of each cell."""
+        u = self._chk(u)
+        flags = np.zeros(self.nx * self.ny, dtype=np.uint8)
+        ratio = np.zeros(self.nx * self.ny)
+        near = ctypes.c_long(0)
+        nf = lib().or_flag_kxrcf(self._ref(), _dp(u), flags.ctypes.data_as(_U8), ctypes.byref(near), _dp(ratio))
+        return flags, int(nf), int(near.value), ratio
+
+    def step_ind(self, u, dt, indicator="tvb", M=0.01, limit=True, eps=1e-6, pp=False, pp_eps=1e-13):
+        """SSP-RK3 step with indicator "tvb" or "kxrcf" (and the optional positivity scaling).
+        Returns (u_new, n_flagged, n_near, n_changed, n_bad)."""
+        ind = {"tvb": 0, "kxrcf": 2}[indicator]
+        u = self._chk(u).copy()
+        near, npp, bad = ctypes.c_long(0), ctypes.c_long(0), ctypes.c_long(0)
+        nf = lib().or_step_ind(self._ref(), dt, _dp(u), ind, M, int(limit), eps, int(pp), pp_eps,
+                               ctypes.byref(near), ctypes.byref(npp), ctypes.byref(bad))
+        return u, int(nf), int(near.value), int(npp.value), int(bad.value)
 
     def positivity_limit(self, u, eps0=1e-13):
         """Zhang-Shu positivity-preserving scaling (Euler). Returns (u_new, cells changed,

@@ -705,6 +705,146 @@ long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* fla
 }
 
 /* ------------------------------------------------------------------------------------
+ * KXRCF troubled-cell indicator (Sec. 3, step 1: the paper's own choice, after
+ * Krivodonova et al., ref. [kxrcf]).  For an indicator variable w of cell j,
+ *   I_j = | int_{dI_j^-} (w_j - w_nb) ds | / ( r^{(N+1)/2} |dI_j^-| ||w_j|| ),
+ * dI_j^- the inflow part of the boundary, r the radius of the circle circumscribing the
+ * cell, ||w_j|| the largest |w_j| over the cell's (N+1)^dim Gauss points; the cell is
+ * troubled when I_j > 1.  Readings (the paper prints no formula): inflow faces are those
+ * whose outward normal has a negative product with the mean velocity (Euler m/rho, its
+ * sign taken from the mean momentum; Burgers f'(ubar) = ubar in every direction); a
+ * face integral is the (N+1)-point Gauss rule along the face (a point value in 1D, where
+ * |dI^-| counts inflow faces); the indicator variables are u for Burgers and the density
+ * and the total energy for Euler (either one flags the cell); neighbours follow the
+ * boundary condition as in the scheme.  The decision is num > den without a division,
+ * and near (reporting) when the two are within 8192 ulp.
+ * ----------------------------------------------------------------------------------*/
+static void kx_ratio(double an, double den, double* r) {
+  const double q = den > 0.0 ? an / den : (an > 0.0 ? INFINITY : 0.0);
+  if (q > *r) *r = q;
+}
+
+/* ratio (optional): the largest I_j over the indicator variables (0 without inflow). */
+long or_flag_kxrcf(const or_mesh* m, const double* u, unsigned char* flags, long* n_near, double* ratio) {
+  const int N = m->N, nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, N);
+  or_dg_tables t;
+  dg_tables(N, N + 1, &t);
+  const int nq = N + 1;
+  const int wv[2] = {0, nv - 1};
+  const int nw = m->pde == 0 ? 1 : 2;
+  long nf = 0, nn = 0;
+  if (m->dim == 1) {
+    const double h = (m->xR - m->xL) / m->nx;
+    const double hp = pow(0.5 * h, 0.5 * (N + 1));
+    for (int c = 0; c < m->nx; ++c) {
+      double uc[OR_MAXV * 4], ul[OR_MAXV * 4], ur[OR_MAXV * 4];
+      cell_modes(m, u, c, 0, uc);
+      cell_modes(m, u, c - 1, 0, ul);
+      cell_modes(m, u, c + 1, 0, ur);
+      /* mean velocity sign: Burgers ubar, Euler mbar (rho > 0) */
+      const double vel = m->pde == 0 ? uc[0] : uc[np];
+      int fl = 0, near = 0;
+      double rmax = 0.0;
+      for (int iw = 0; iw < nw; ++iw) {
+        const int v = wv[iw];
+        double num = 0.0, len = 0.0;
+        if (vel > 0.0) { /* left face x = -1 is inflow */
+          double a = 0.0, b = 0.0;
+          for (int k = 0; k < np; ++k) a += uc[v * np + k] * t.Pm[k];
+          for (int k = 0; k < np; ++k) b += ul[v * np + k] * t.Pp[k];
+          num += a - b;
+          len += 1.0;
+        }
+        if (vel < 0.0) { /* right face x = +1 */
+          double a = 0.0, b = 0.0;
+          for (int k = 0; k < np; ++k) a += uc[v * np + k] * t.Pp[k];
+          for (int k = 0; k < np; ++k) b += ur[v * np + k] * t.Pm[k];
+          num += a - b;
+          len += 1.0;
+        }
+        if (len == 0.0) continue;
+        double nrm = 0.0;
+        for (int q = 0; q < nq; ++q) {
+          double a = 0.0;
+          for (int k = 0; k < np; ++k) a += uc[v * np + k] * t.P[q][k];
+          if (fabs(a) > nrm) nrm = fabs(a);
+        }
+        const double den = hp * len * nrm, an = fabs(num);
+        if (ulp_near(an, den)) near = 1;
+        if (an > den) fl = 1;
+        kx_ratio(an, den, &rmax);
+      }
+      if (ratio) ratio[c] = rmax;
+      flags[c] = (unsigned char)fl;
+      nf += fl;
+      nn += near;
+    }
+  } else {
+    const double hx = (m->xR - m->xL) / m->nx, hy = (m->yR - m->yL) / m->ny;
+    const double hp = pow(0.5 * sqrt(hx * hx + hy * hy), 0.5 * (N + 1));
+    int A[OR_MAXNP], Bm[OR_MAXNP];
+    for (int k = 0; k < np; ++k) mode_ab(k, &A[k], &Bm[k]);
+    for (int iy = 0; iy < m->ny; ++iy)
+      for (int ix = 0; ix < m->nx; ++ix) {
+        double uc[OR_MAXV * OR_MAXNP], nb[4][OR_MAXV * OR_MAXNP];
+        cell_modes(m, u, ix, iy, uc);
+        cell_modes(m, u, ix - 1, iy, nb[0]);
+        cell_modes(m, u, ix + 1, iy, nb[1]);
+        cell_modes(m, u, ix, iy - 1, nb[2]);
+        cell_modes(m, u, ix, iy + 1, nb[3]);
+        const double vx = m->pde == 0 ? uc[0] : uc[np], vy = m->pde == 0 ? uc[0] : uc[2 * np];
+        /* faces W, E, S, N: inflow test, face length, own side, neighbour side */
+        const int in[4] = {vx > 0.0, vx < 0.0, vy > 0.0, vy < 0.0};
+        const double flen[4] = {hy, hy, hx, hx};
+        int fl = 0, near = 0;
+        double rmax = 0.0;
+        for (int iw = 0; iw < nw; ++iw) {
+          const int v = wv[iw];
+          double num = 0.0, len = 0.0;
+          for (int f = 0; f < 4; ++f) {
+            if (!in[f]) continue;
+            double s = 0.0;
+            for (int q = 0; q < nq; ++q) {
+              double a = 0.0, b = 0.0;
+              for (int k = 0; k < np; ++k) {
+                /* own face point and the neighbour's matching point */
+                double po, pn;
+                if (f == 0) { po = t.Pm[A[k]] * t.P[q][Bm[k]]; pn = t.Pp[A[k]] * t.P[q][Bm[k]]; }
+                else if (f == 1) { po = t.Pp[A[k]] * t.P[q][Bm[k]]; pn = t.Pm[A[k]] * t.P[q][Bm[k]]; }
+                else if (f == 2) { po = t.P[q][A[k]] * t.Pm[Bm[k]]; pn = t.P[q][A[k]] * t.Pp[Bm[k]]; }
+                else { po = t.P[q][A[k]] * t.Pp[Bm[k]]; pn = t.P[q][A[k]] * t.Pm[Bm[k]]; }
+                a += uc[v * np + k] * po;
+                b += nb[f][v * np + k] * pn;
+              }
+              s += t.w[q] * (a - b);
+            }
+            num += s * (0.5 * flen[f]);
+            len += flen[f];
+          }
+          if (len == 0.0) continue;
+          double nrm = 0.0;
+          for (int qx = 0; qx < nq; ++qx)
+            for (int qy = 0; qy < nq; ++qy) {
+              double a = 0.0;
+              for (int k = 0; k < np; ++k) a += uc[v * np + k] * (t.P[qx][A[k]] * t.P[qy][Bm[k]]);
+              if (fabs(a) > nrm) nrm = fabs(a);
+            }
+          const double den = hp * len * nrm, an = fabs(num);
+          if (ulp_near(an, den)) near = 1;
+          if (an > den) fl = 1;
+          kx_ratio(an, den, &rmax);
+        }
+        if (ratio) ratio[(size_t)iy * m->nx + ix] = rmax;
+        flags[(size_t)iy * m->nx + ix] = (unsigned char)fl;
+        nf += fl;
+        nn += near;
+      }
+  }
+  if (n_near) *n_near = nn;
+  return nf;
+}
+
+/* ------------------------------------------------------------------------------------
  * Local characteristic decomposition for the Euler systems (Sec. 3, "local
  * characteristic field decomposition"): right/left eigenvectors of the flux Jacobian
  * in direction dir at the state u (conserved).  R columns, L rows, L R = I.
@@ -1131,11 +1271,12 @@ long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) 
   return changed;
 }
 
-/* One SSP-RK3 step as or_step, with the positivity-preserving scaling after the limiter
- * of every stage when pp is set (Euler).  *n_pp (if given) receives the number of cell
- * changes over the three stages and *n_bad the cells whose mean was not admissible. */
-long or_step_pp(const or_mesh* m, double dt, double* u, double M, int limit, double eps, int pp, double pp_eps,
-                long* n_near, long* n_pp, long* n_bad) {
+/* One SSP-RK3 step as or_step with the indicator ind (0 TVB with constant M, 2 KXRCF)
+ * and, when pp is set (Euler), the positivity-preserving scaling after the limiter of
+ * every stage.  *n_pp (if given) receives the number of cell changes over the three
+ * stages and *n_bad the cells whose mean was not admissible. */
+long or_step_ind(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,
+                 double pp_eps, long* n_near, long* n_pp, long* n_bad) {
   size_t ncell = (size_t)m->nx * m->ny;
   size_t n = ncell * or_nvars(m->dim, m->pde) * or_nmodes(m->dim, m->N);
   double* un = (double*)malloc(n * sizeof(double));
@@ -1149,7 +1290,7 @@ long or_step_pp(const or_mesh* m, double dt, double* u, double M, int limit, dou
   for (int s = 1; s <= 3; ++s) {
     or_rk_stage(m, s, dt, un, prev, a);
     if (limit) {
-      nf += or_flag_tvb(m, a, M, fl, &near);
+      nf += ind == 2 ? or_flag_kxrcf(m, a, fl, &near, NULL) : or_flag_tvb(m, a, M, fl, &near);
       nn += near;
       or_csweno_limit(m, a, fl, b, eps);
       double* t = a; a = b; b = t;
@@ -1167,6 +1308,11 @@ long or_step_pp(const or_mesh* m, double dt, double* u, double M, int limit, dou
   if (n_bad) *n_bad = nb;
   free(un); free(keep); free(a); free(b); free(fl);
   return nf;
+}
+
+long or_step_pp(const or_mesh* m, double dt, double* u, double M, int limit, double eps, int pp, double pp_eps,
+                long* n_near, long* n_pp, long* n_bad) {
+  return or_step_ind(m, dt, u, 0, M, limit, eps, pp, pp_eps, n_near, n_pp, n_bad);
 }
 
 /* ------------------------------------------------------------------------------------
