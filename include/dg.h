@@ -47,7 +47,7 @@ typedef enum {
 
 typedef enum { DG_BURGERS = 0, DG_EULER = 1 } dg_pde;
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 } dg_bc;
-typedef enum { DG_IND_TVB = 0, DG_IND_MLP = 1 } dg_indicator;
+typedef enum { DG_IND_TVB = 0, DG_IND_MLP = 1, DG_IND_KXRCF = 2 } dg_indicator;
 
 /* Initial-condition families for dg_project_ic (parameters per instance):
  *   DG_IC_SINE          u = p0 + p1 sin(p2 x + p3 y)                              (4)
@@ -105,8 +105,13 @@ dg_status dg_set_dt(dg_mesh* m, const double* dt);
  * Errors: DG_EINVAL (stage not 1..3), DG_ESTATE (stage s without stage s-1 before it). */
 dg_status dg_rk_stage(dg_mesh* m, int stage, double dt);
 
-/* Troubled-cell indicator on the current state (Sec. 3, step 1; the method here uses the
- * TVB modified minmod with constant tvb_M instead of the paper's KXRCF).  Writes the
+/* Troubled-cell indicator on the current state (Sec. 3, step 1).  DG_IND_TVB: the TVB
+ * modified minmod with constant tvb_M on the face values of every variable, per
+ * direction.  DG_IND_KXRCF: the paper's own choice (Krivodonova et al.), troubled when
+ * |int over the inflow faces of (w_j - w_nb)| > r^((N+1)/2) |inflow faces| max|w_j| over
+ * the cell's Gauss points, r the circumscribed radius, inflow by the sign of the mean
+ * velocity, w = u (Burgers) or density and total energy (Euler); tvb_M is ignored.
+ * DG_IND_MLP: the TVB flags the learned network keeps (dg_set_indicator_mlp).  Writes the
  * device flag array and the compacted list of troubled cells used by dg_cswenolimit.
  * n_flagged, n_near (cells whose deciding comparison lies within 1e-12 relative of the
  * threshold) and flags_out (host, one byte per cell) are optional; asking for any of them

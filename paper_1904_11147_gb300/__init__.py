@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libcswenodg.so")
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EPOSITIVITY, DG_ETIMEOUT, DG_ESTATE = range(7)
 BURGERS, EULER = 0, 1
 BC_PERIODIC, BC_OUTFLOW = 0, 1
-IND_TVB, IND_MLP = 0, 1
+IND_TVB, IND_MLP, IND_KXRCF = 0, 1, 2
 IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
 STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EPOSITIVITY",
                 5: "DG_ETIMEOUT", 6: "DG_ESTATE"}

@@ -71,6 +71,9 @@ void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* p
                             double gam, const int* lc, const int* li, const Counters* cnt, const unsigned char* flags,
                             int skip_kept, unsigned int* fail, int nblocks);
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total);
+void launch_kxrcf(int dim, int pde, int N, const LaunchArgs& a, const double* hpow, const double* psi_m1,
+                  const double* psi_p1, const double* psi_q, const double* gw, unsigned char* flags, Counters* cnt,
+                  int* lc, int* li);
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* phi, int npt, double c0, double gam, double eps0,
                        unsigned long long* counts, int nblocks);
@@ -180,6 +183,10 @@ struct dg_mesh {
   unsigned long long* pp_counts = nullptr;
   bool g_pp = false;
   double g_pp_eps = 0.0;
+  // KXRCF indicator: r^((N+1)/2) per instance (r the circumscribed radius) and the basis
+  // values at r = -1, +1 and at the Gauss points, with the Gauss weights
+  double* d_kx_hpow = nullptr;
+  double kx_pm[4], kx_pp[4], kx_pq[16], kx_w[4];
 };
 
 static size_t mesh_doubles(const dg_mesh* m) { return (size_t)m->ncell * m->V * m->NP; }
@@ -208,6 +215,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
   cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->save); cudaFree(m->fail); cudaFree(m->pos_counts);
   cudaFree(m->pp_counts);
+  cudaFree(m->d_kx_hpow);
   delete m;
   return DG_OK;
 }
@@ -339,7 +347,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->list_inst, sizeof(int) * m->ctot) && alloc((void**)&m->cnt, sizeof(Counters)) &&
             alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst) &&
             alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long)) &&
-            alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long));
+            alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long)) &&
+            alloc((void**)&m->d_kx_hpow, sizeof(double) * n_inst);
   if (!ok) {
     cudaGetLastError();
     dg_mesh_destroy(m);
@@ -352,6 +361,22 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (e == cudaSuccess) e = cudaMemset(m->cnt, 0, sizeof(Counters));
   if (e == cudaSuccess) e = cudaMemset(m->flag_totals, 0, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(m->pp_counts, 0, 2 * sizeof(unsigned long long));
+  {
+    std::vector<double> hp(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      const Inst& I = m->h_inst[i];
+      const double r = dim == 1 ? 0.5 * I.hx : 0.5 * std::sqrt(I.hx * I.hx + I.hy * I.hy);
+      hp[i] = std::pow(r, 0.5 * (N + 1));
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_kx_hpow, hp.data(), sizeof(double) * n_inst, cudaMemcpyHostToDevice);
+    const dgt::Tabs& tb = g_tabs[N - 1];
+    for (int k = 0; k <= N; ++k) {
+      m->kx_pm[k] = tb.psi_m1[k];
+      m->kx_pp[k] = tb.psi_p1[k];
+      m->kx_w[k] = tb.gw[k];
+      for (int q = 0; q <= N; ++q) m->kx_pq[q * (N + 1) + k] = tb.psi_q[q][k];
+    }
+  }
   if (e != cudaSuccess) {
     dg_mesh_destroy(m);
     return fail(DG_ECUDA, "mesh upload: %s", cudaGetErrorString(e));
@@ -488,6 +513,12 @@ static cudaError_t learned_limit(dg_mesh* m) {
   launch_count_fail(m->st, fail2, m->n_inst, m->pos_counts + 1);
   m->launches += 9;
   return cudaSuccess;
+}
+
+static void k_flag_kx(dg_mesh* m) {
+  launch_kxrcf(m->dim, m->pde, m->N, args<LaunchArgs>(m, 0, m->cur, m->cur), m->d_kx_hpow, m->kx_pm, m->kx_pp,
+               m->kx_pq, m->kx_w, m->flags, m->cnt, m->list_cell, m->list_inst);
+  m->launches++;
 }
 
 static void k_flag(dg_mesh* m, double M) {
@@ -645,11 +676,15 @@ extern "C" dg_status dg_rk_stage(dg_mesh* m, int stage, double dt) {
 extern "C" dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flagged, int64_t* n_near,
                                    uint8_t* flags_out) {
   if (!m) return fail(DG_EINVAL, "null mesh");
-  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP) return fail(DG_EINVAL, "unknown indicator %d", indicator);
+  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP && indicator != DG_IND_KXRCF)
+    return fail(DG_EINVAL, "unknown indicator %d", indicator);
   if (indicator == DG_IND_MLP && !m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
   if (!(tvb_M >= 0.0)) return fail(DG_EINVAL, "tvb_M must be >= 0");
   if (indicator == DG_IND_MLP) {
     CK(learned_flags(m, tvb_M));
+  } else if (indicator == DG_IND_KXRCF) {
+    CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
+    k_flag_kx(m);
   } else {
     CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
     k_flag(m, tvb_M);
@@ -734,7 +769,8 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
       k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt_b, m->pde == DG_EULER ? m->cnt_c : nullptr, m->flag_totals);
     } else {
       CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
-      k_flag(m, M);
+      if (indicator == DG_IND_KXRCF) k_flag_kx(m);
+      else k_flag(m, M);
       k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
       k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt, nullptr, m->flag_totals);
     }
@@ -747,7 +783,8 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
 
 extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M) {
   if (!m) return fail(DG_EINVAL, "null mesh");
-  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP) return fail(DG_EINVAL, "unknown indicator %d", indicator);
+  if (indicator != DG_IND_TVB && indicator != DG_IND_MLP && indicator != DG_IND_KXRCF)
+    return fail(DG_EINVAL, "unknown indicator %d", indicator);
   if (indicator == DG_IND_MLP && !m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
   if (m->last_stage != 0 && m->last_stage != 3) return fail(DG_ESTATE, "a step was left unfinished (stage %d)", m->last_stage);
   // the graph reads the per-instance time steps from device memory

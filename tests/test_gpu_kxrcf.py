@@ -1,0 +1,86 @@
+"""The KXRCF indicator (DG_IND_KXRCF) against the oracle: flags on random states of every
+kind, stage-by-stage runs with it, and the shock tubes with the paper's own indicator."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.exact import l1_linf_1d, riemann_exact
+import paper_1904_11147_gb300 as dgl
+from paper_1904_11147_gb300 import workloads as W
+from shadow_util import shadow_stages
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(d, p, n) for d in (1, 2) for p in (0, 1) for n in (1, 2, 3)]
+
+
+@pytest.mark.parametrize("dim,pde,N", CASES)
+@pytest.mark.parametrize("bc", [0, 1])
+def test_kxrcf_flags_parity(dim, pde, N, bc):
+    nx, ny = (613, 1) if dim == 1 else (70, 45)
+    o = oracle.Mesh(dim, pde, N, nx, ny, box=(0.0, 1.3, 0.0, 0.9), bc=bc)
+    g = dgl.Mesh(dim, pde, N, [nx], [ny], [(0.0, 1.3, 0.0, 0.9)], bc=bc)
+    rng = np.random.default_rng(500 + 10 * dim + 3 * pde + N)
+    # a smooth projected field (mostly unflagged) with 5 % of the cells scaled by 1.3
+    ky = 2 * np.pi if dim == 2 else 0.0
+    if pde == 0:
+        u = o.project_ic(W.IC_SINE, [2.0, 0.5, 2 * np.pi, ky])
+    else:
+        u = o.project_ic(W.IC_DENSITY_WAVE, [1.0, 0.2, 2 * np.pi, ky, 0.3, -0.2, 1.0])
+    u[rng.uniform(size=nx * ny) < 0.05] *= 1.3
+    g.set_modes(u)
+    fl, nf, nn = g.flag_cells(dgl.IND_KXRCF, 0.0, want=True)
+    fo, nfo, nno, ratio = o.flag_kxrcf(u)
+    diff = int((fl != fo).sum())
+    assert diff <= nno and abs(nn - nno) <= diff + nno, (diff, nn, nno)
+    assert 0 < nfo < nx * ny  # both kinds of cells present
+    # the limiter then works on the list the indicator compacted
+    g.cswenolimit()
+    ref = o.limit(u, fl)
+    assert np.abs(g.get_modes() - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name,steps", [("quadrant_p2_40", 40), ("quadrant_p3_24", 30), ("burgers2d_p2_32", 40)])
+def test_kxrcf_shadow_2d(name, steps):
+    import torch
+    st = torch.cuda.Stream()
+    if name.startswith("quadrant"):
+        N = 2 if "p2" in name else 3
+        n = 40 if N == 2 else 24
+        w = W.euler_2d_quadrant(n, N, seed=1907 if N == 3 else 1904)
+        o = oracle.Mesh(2, 1, N, n, n, box=w.box[0], bc=w.bc)
+        g = dgl.Mesh(2, 1, N, [n], [n], w.box, bc=w.bc, stream=st.cuda_stream)
+        u0 = o.project_ic(w.ic, w.params[0])
+        ws = o.max_wavespeed(u0)
+        dt = 0.1 / (ws[0] * n + ws[1] * n)
+    else:
+        w = W.burgers_2d_batched(1, 2, 32, 32)
+        o = oracle.Mesh(2, 0, 2, 32, 32, box=w.box[0], bc=w.bc)
+        g = dgl.Mesh(2, 0, 2, [32], [32], w.box, bc=w.bc, stream=st.cuda_stream)
+        u0 = o.project_ic(w.ic, w.params[0])
+        dt = 0.1 / (2 * 1.6 / (4.0 / 32))
+    with torch.cuda.stream(st):
+        ws_, wl, nf, done, _ = shadow_stages(o, g, u0, dt, steps, indicator="kxrcf")
+    print(name, "KXRCF: worst stage %.2e, worst limited %.2e, flagged %d" % (ws_, wl, nf))
+    assert done == steps and (nf > 0 or name.startswith("burgers"))  # Burgers: no shock yet
+
+
+@pytest.mark.parametrize("kind,t_end,l1_max", [("sod", 0.2, 3e-3), ("lax", 0.13, 4e-3)])
+def test_kxrcf_shock_tubes_p3_k800(kind, t_end, l1_max):
+    """Sod and Lax to the paper's end times (Lax at t = 0.13, which the TVB-indicator run
+    does not reach with P3) at K = 800, P3, with the KXRCF indicator."""
+    import torch
+    st = torch.cuda.Stream()
+    w = W.shock_tube(kind, 800, 3)
+    o = oracle.Mesh(1, 1, 3, 800, box=w.box[0], bc=w.bc)
+    g = dgl.Mesh(1, 1, 3, [800], None, w.box, bc=w.bc, stream=st.cuda_stream)
+    u0 = o.project_ic(w.ic, w.params[0])
+    dt = lambda k, u: 0.1 * (1.0 / 800) / o.max_wavespeed(u)[0]
+    with torch.cuda.stream(st):
+        ws, wl, nf, k, t = shadow_stages(o, g, u0, dt, 100000, t_end=t_end, graph_check=False, indicator="kxrcf")
+    assert abs(t - t_end) < 1e-12
+    WL, WR = w.params[0][0:3], w.params[0][3:6]
+    l1, _ = l1_linf_1d(o, g.get_modes(), lambda x: riemann_exact(WL, WR, 1.4, (x - 0.5) / t_end)[0])
+    print("%s KXRCF: %d steps, worst stage %.2e, worst limited %.2e, flagged per stage %.1f, density L1 %.2e"
+          % (kind, k, ws, wl, nf / (3 * k), l1))
+    assert l1 < l1_max
