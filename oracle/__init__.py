@@ -83,6 +83,12 @@ def lib():
             l.or_project_ic.argtypes = [M, ctypes.c_int, _D, _D]
             l.or_euler_eigen.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D, _D]
             l.or_weno_export.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, _I, _D]
+            l.or_weno_export_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D,
+                                           _D, _I, _D]
+            l.or_parent_weno_limit.argtypes = [M, _D, _U8, _D, ctypes.c_double]
+            l.or_step_gen.argtypes = [M, ctypes.c_double, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, _L, _L, _L]
+            l.or_step_gen.restype = ctypes.c_long
             l.or_dg_export.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
             _lib = l
     return _lib
@@ -185,6 +191,25 @@ class Mesh:
         nf = lib().or_flag_kxrcf(self._ref(), _dp(u), flags.ctypes.data_as(_U8), ctypes.byref(near), _dp(ratio))
         return flags, int(nf), int(near.value), ratio
 
+    def parent_limit(self, u, flags, eps=1e-6):
+        """Parent WENO limiter (whole cells j-N..j+N) on the flagged cells (Jacobi)."""
+        u = self._chk(u)
+        out = np.empty_like(u)
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        lib().or_parent_weno_limit(self._ref(), _dp(u), fl.ctypes.data_as(_U8), _dp(out), eps)
+        return out
+
+    def step_gen(self, u, dt, indicator="tvb", limiter="csweno", M=0.01, eps=1e-6, pp=False, pp_eps=1e-13):
+        """SSP-RK3 step with indicator "tvb"/"kxrcf" and limiter "csweno"/"parent"/"none".
+        Returns (u_new, n_flagged, n_near, n_changed, n_bad)."""
+        ind = {"tvb": 0, "kxrcf": 2}[indicator]
+        lim = {"none": 0, "csweno": 1, "parent": 2}[limiter]
+        u = self._chk(u).copy()
+        near, npp, bad = ctypes.c_long(0), ctypes.c_long(0), ctypes.c_long(0)
+        nf = lib().or_step_gen(self._ref(), dt, _dp(u), ind, M, lim, eps, int(pp), pp_eps, ctypes.byref(near),
+                               ctypes.byref(npp), ctypes.byref(bad))
+        return u, int(nf), int(near.value), int(npp.value), int(bad.value)
+
     def step_ind(self, u, dt, indicator="tvb", M=0.01, limit=True, eps=1e-6, pp=False, pp_eps=1e-13):
         """SSP-RK3 step with indicator "tvb" or "kxrcf" (and the optional positivity scaling).
         Returns (u_new, n_flagged, n_near, n_changed, n_bad)."""
@@ -236,10 +261,12 @@ def euler_eigen(dim, gamma, direction, u):
     return R, L
 
 
-def weno_tables(N: int):
-    """The CSWENO tables the oracle derived for degree N (Sec. 3, Steps 1-4)."""
+def weno_tables(N: int, parent: bool = False, points=None):
+    """The CSWENO tables the oracle derived for degree N (Sec. 3, Steps 1-4); parent: the
+    full-width stencil of the parent WENO limiter; points: reconstruction points r in
+    [-1, 1] instead of the Step 1 points."""
     ns = 2 * N + 1
-    ng = 2 if N == 1 else 4
+    ng = (2 if N == 1 else 4) if points is None else len(points)
     pt, wt = np.zeros(ng), np.zeros(ng)
     C = np.zeros((N + 1, ng, ns))
     D = np.zeros((ng, ns))
@@ -248,8 +275,9 @@ def weno_tables(N: int):
     SA = np.zeros((ns, N + 1))
     OFF = np.zeros(ns, dtype=np.int32)
     resid = ctypes.c_double(0)
-    lib().or_weno_export(N, _dp(pt), _dp(wt), _dp(C), _dp(D), _dp(gam), _dp(B), _dp(SA),
-                         OFF.ctypes.data_as(_I), ctypes.byref(resid))
+    rin = np.ascontiguousarray(points if points is not None else [0.0], dtype=np.float64)
+    lib().or_weno_export_g(N, int(parent), 0 if points is None else ng, _dp(rin), _dp(pt), _dp(wt), _dp(C), _dp(D),
+                           _dp(gam), _dp(B), _dp(SA), OFF.ctypes.data_as(_I), ctypes.byref(resid))
     return dict(pt=pt, wt=wt, C=C, D=D, gam=gam, B=B, SA=SA, OFF=OFF, resid=resid.value)
 
 

@@ -172,13 +172,17 @@ typedef struct {
   double gam_resid;                   /* max residual of the full Eq. (8) system */
 } or_weno_tables;
 
-/* edges of the 2N+1 stencil cells in xi units */
-static void stencil_edges(int N, ld* e) {
-  int ns = 2 * N + 1;
+/* edges of the 2N+1 stencil cells in xi units (troubled cell [-1/2, 1/2]).  CSWENO: the
+ * immediate neighbours split into N equal parts (Fig. 1).  Parent WENO (the limiter of
+ * Qiu and Shu the paper compares with, ref. [qs1]): the whole cells j-N..j+N. */
+static void stencil_edges(int N, int parent, ld* e) {
+  if (parent) {
+    for (int k = 0; k <= 2 * N + 1; ++k) e[k] = -(ld)N - 0.5L + k;
+    return;
+  }
   for (int k = 0; k <= N; ++k) e[k] = -1.5L + (ld)k / N;           /* left neighbour */
   e[N + 1] = 0.5L;                                                  /* troubled cell */
   for (int k = 1; k <= N; ++k) e[N + 1 + k] = 0.5L + (ld)k / N;     /* right neighbour */
-  (void)ns;
 }
 
 /* Rows r (over the cells first..first+n-1) with  value_at(xi_g) = r . averages  for the
@@ -208,15 +212,20 @@ static void recon_rows(int n, const ld* e, int first, int ng, const ld* xig, ld*
   }
 }
 
-void or_weno_tables_build(int N, or_weno_tables* t) {
+/* parent: full-width stencil (see stencil_edges).  ng_in > 0: reconstruct at the ng_in
+ * points r_in instead of the Step 1 points (tables for tests; weights then unused). */
+static void weno_tables_build_g(int N, int parent, int ng_in, const double* r_in, or_weno_tables* t) {
   memset(t, 0, sizeof(*t));
   int ns = 2 * N + 1, ng;
   ld e[OR_MAXS + 1], r[OR_MAXG], w[OR_MAXG], xi[OR_MAXG];
   t->N = N;
   t->ns = ns;
-  stencil_edges(N, e);
+  stencil_edges(N, parent, e);
   /* Step 1: the points the paper prescribes, weights of the matching rule. */
-  if (N == 1) {
+  if (ng_in > 0) {
+    ng = ng_in;
+    for (int g = 0; g < ng; ++g) r[g] = r_in[g];
+  } else if (N == 1) {
     ng = 2;
     r[0] = -1.0L / sqrtl(3.0L); r[1] = -r[0];
   } else if (N == 2) {
@@ -229,7 +238,9 @@ void or_weno_tables_build(int N, or_weno_tables* t) {
     r[2] = -r[1]; r[3] = -r[0];
   }
   for (int g = 0; g < ng; ++g) {
-    if (N == 2) { /* Lobatto weights 2/(n(n-1) P_{n-1}(x)^2), n = 4 */
+    if (ng_in > 0) {
+      w[g] = 0.0L;
+    } else if (N == 2) { /* Lobatto weights 2/(n(n-1) P_{n-1}(x)^2), n = 4 */
       ld p = legP(3, r[g]);
       w[g] = 2.0L / (12.0L * p * p);
     } else { /* Gauss weights 2/((1-x^2) P_n'(x)^2) */
@@ -309,6 +320,11 @@ void or_weno_tables_build(int N, or_weno_tables* t) {
    * of the right neighbour, each in its own reference coordinate. */
   for (int k = 0; k < ns; ++k) {
     ld a, b;
+    if (parent) { /* whole cell j + k - N: its average is U_0 psi_0 */
+      t->OFF[k] = k - N;
+      for (int n = 0; n <= N; ++n) t->SA[k][n] = n == 0 ? (double)psi_avg(0, -1.0L, 1.0L) : 0.0;
+      continue;
+    }
     if (k < N) { a = -1.0L + 2.0L * k / N; b = -1.0L + 2.0L * (k + 1) / N; t->OFF[k] = -1; }
     else if (k == N) { a = -1.0L; b = 1.0L; t->OFF[k] = 0; }
     else { int q = k - N - 1; a = -1.0L + 2.0L * q / N; b = -1.0L + 2.0L * (q + 1) / N; t->OFF[k] = 1; }
@@ -317,6 +333,8 @@ void or_weno_tables_build(int N, or_weno_tables* t) {
       for (int n = 1; n <= N; ++n) t->SA[k][n] = 0.0; /* orthogonality to psi_0 */
   }
 }
+
+void or_weno_tables_build(int N, or_weno_tables* t) { weno_tables_build_g(N, 0, 0, NULL, t); }
 
 /* ------------------------------------------------------------------------------------
  * DG tables for the weak form (Eqs. (5)-(7)): (N+1)-point Gauss rule (our reading; the
@@ -404,7 +422,9 @@ static void llf(int dim, int pde, double gam, int dir, const double* uL, const d
 /* ------------------------------------------------------------------------------------
  * Neighbour access with boundary conditions.  Periodic wraps.  Outflow (our reading of
  * the transmissive boundaries of Examples 7-8): the ghost cell holds the mirror image
- * of the boundary cell's polynomial, i.e. modes odd in the normal direction negated.
+ * of the boundary cell's polynomial, i.e. modes odd in the normal direction negated;
+ * further ghosts (the parent WENO stencil reaches N cells out) mirror the interior cell
+ * at the reflected position (ghost -1-k <-> cell k).
  * ----------------------------------------------------------------------------------*/
 static void cell_modes(const or_mesh* m, const double* u, int ix, int iy, double* out) {
   int nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, m->N);
@@ -413,10 +433,15 @@ static void cell_modes(const or_mesh* m, const double* u, int ix, int iy, double
     ix = (ix % m->nx + m->nx) % m->nx;
     iy = (iy % m->ny + m->ny) % m->ny;
   } else {
-    if (ix < 0) { ix = 0; fx = 1; }
-    if (ix >= m->nx) { ix = m->nx - 1; fx = 1; }
-    if (iy < 0) { iy = 0; fy = 1; }
-    if (iy >= m->ny) { iy = m->ny - 1; fy = 1; }
+    /* ghost -1-k is the mirror image of cell k (reflection across the boundary) */
+    if (ix < 0) { ix = -1 - ix; fx = 1; }
+    if (ix >= m->nx) { ix = 2 * m->nx - 1 - ix; fx = 1; }
+    if (iy < 0) { iy = -1 - iy; fy = 1; }
+    if (iy >= m->ny) { iy = 2 * m->ny - 1 - iy; fy = 1; }
+    if (ix < 0) ix = 0;
+    if (ix >= m->nx) ix = m->nx - 1;
+    if (iy < 0) iy = 0;
+    if (iy >= m->ny) iy = m->ny - 1;
   }
   const double* src = u + ((size_t)iy * m->nx + ix) * nv * np;
   for (int v = 0; v < nv; ++v)
@@ -969,23 +994,25 @@ static void weno_1d(const or_weno_tables* t, const double* avg, double eps, doub
  * Updates are Jacobi: every flagged cell reads the unlimited input u; results go to
  * out (which starts as a copy of u).  eps is the WENO epsilon (1e-6 in the paper).
  * ----------------------------------------------------------------------------------*/
-void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* flags, double* out, double eps) {
+static void weno_limit_g(const or_mesh* m, const double* u, const unsigned char* flags, double* out, double eps,
+                         int parent) {
   int N = m->N, nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, N);
   size_t ncell = (size_t)m->nx * m->ny;
   or_weno_tables t;
-  or_weno_tables_build(N, &t);
+  weno_tables_build_g(N, parent, 0, NULL, &t);
   int ns = t.ns, ng = t.ng;
+  const int reach = parent ? N : 1; /* neighbourhood reach */
   memcpy(out, u, ncell * nv * np * sizeof(double));
   if (m->dim == 1) {
     for (int c = 0; c < m->nx; ++c) {
       if (!flags[c]) continue;
-      double nbm[3][OR_MAXV * 4];
-      for (int d = -1; d <= 1; ++d) cell_modes(m, u, c + d, 0, nbm[d + 1]);
+      double nbm[OR_MAXS][OR_MAXV * 4];
+      for (int d = -reach; d <= reach; ++d) cell_modes(m, u, c + d, 0, nbm[d + reach]);
       /* subcell averages per conserved variable */
       double avg[OR_MAXV][OR_MAXS];
       for (int v = 0; v < nv; ++v)
         for (int k = 0; k < ns; ++k) {
-          const double* src = nbm[t.OFF[k] + 1] + v * np;
+          const double* src = nbm[t.OFF[k] + reach] + v * np;
           double s = 0;
           for (int n = 0; n < np; ++n) s += src[n] * t.SA[k][n];
           avg[v][k] = s;
@@ -993,7 +1020,7 @@ void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* fla
       double val[OR_MAXV][OR_MAXG];
       if (m->pde == 1) {
         double mean[3], R[9], L[9], w[3][OR_MAXS], wv[3][OR_MAXG];
-        for (int v = 0; v < 3; ++v) mean[v] = nbm[1][v * np] * t.SA[N][0];
+        for (int v = 0; v < 3; ++v) mean[v] = nbm[reach][v * np] * t.SA[N][0];
         or_euler_eigen(1, m->gamma, 0, mean, R, L);
         for (int f = 0; f < 3; ++f)
           for (int k = 0; k < ns; ++k) {
@@ -1026,21 +1053,21 @@ void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* fla
     for (int ix = 0; ix < m->nx; ++ix) {
       size_t c = (size_t)iy * m->nx + ix;
       if (!flags[c]) continue;
-      double nbm[3][3][OR_MAXV * OR_MAXNP];
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) cell_modes(m, u, ix + dx, iy + dy, nbm[dy + 1][dx + 1]);
+      double nbm[OR_MAXS][OR_MAXS][OR_MAXV * OR_MAXNP];
+      for (int dy = -reach; dy <= reach; ++dy)
+        for (int dx = -reach; dx <= reach; ++dx) cell_modes(m, u, ix + dx, iy + dy, nbm[dy + reach][dx + reach]);
       /* sub-rectangle averages avg[v][ky][kx] */
       double avg[OR_MAXV][OR_MAXS][OR_MAXS];
       for (int v = 0; v < nv; ++v)
         for (int ky = 0; ky < ns; ++ky)
           for (int kx = 0; kx < ns; ++kx) {
-            const double* src = nbm[t.OFF[ky] + 1][t.OFF[kx] + 1] + v * np;
+            const double* src = nbm[t.OFF[ky] + reach][t.OFF[kx] + reach] + v * np;
             double s = 0;
             for (int k = 0; k < np; ++k) s += src[k] * t.SA[kx][A[k]] * t.SA[ky][Bm[k]];
             avg[v][ky][kx] = s;
           }
       double mean[OR_MAXV];
-      for (int v = 0; v < nv; ++v) mean[v] = nbm[1][1][v * np] * t.SA[N][0] * t.SA[N][0];
+      for (int v = 0; v < nv; ++v) mean[v] = nbm[reach][reach][v * np] * t.SA[N][0] * t.SA[N][0];
       double Rx[16], Lx[16], Ry[16], Ly[16];
       if (m->pde == 1) {
         or_euler_eigen(2, m->gamma, 0, mean, Rx, Lx);
@@ -1104,6 +1131,18 @@ void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* fla
           out[(c * nv + v) * np + k] = s;
         }
     }
+}
+
+void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* flags, double* out, double eps) {
+  weno_limit_g(m, u, flags, out, eps, 0);
+}
+
+/* The parent WENO limiter of Qiu and Shu (ref. [qs1]), the paper's main comparison (Sec.
+ * 4): the same reconstruction as or_csweno_limit on the whole cells j-N..j+N (their cell
+ * averages) instead of subcells of the immediate neighbours; in 2D on the (2N+1)^2 cell
+ * averages around the troubled cell.  Needs N cells on each side (ghosts reflect). */
+void or_parent_weno_limit(const or_mesh* m, const double* u, const unsigned char* flags, double* out, double eps) {
+  weno_limit_g(m, u, flags, out, eps, 1);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -1275,7 +1314,15 @@ long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) 
  * and, when pp is set (Euler), the positivity-preserving scaling after the limiter of
  * every stage.  *n_pp (if given) receives the number of cell changes over the three
  * stages and *n_bad the cells whose mean was not admissible. */
+long or_step_gen(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,
+                 double pp_eps, long* n_near, long* n_pp, long* n_bad);
 long or_step_ind(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,
+                 double pp_eps, long* n_near, long* n_pp, long* n_bad) {
+  return or_step_gen(m, dt, u, ind, M, limit, eps, pp, pp_eps, n_near, n_pp, n_bad);
+}
+
+/* limit: 0 none, 1 CSWENO, 2 parent WENO */
+long or_step_gen(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,
                  double pp_eps, long* n_near, long* n_pp, long* n_bad) {
   size_t ncell = (size_t)m->nx * m->ny;
   size_t n = ncell * or_nvars(m->dim, m->pde) * or_nmodes(m->dim, m->N);
@@ -1292,7 +1339,8 @@ long or_step_ind(const or_mesh* m, double dt, double* u, int ind, double M, int 
     if (limit) {
       nf += ind == 2 ? or_flag_kxrcf(m, a, fl, &near, NULL) : or_flag_tvb(m, a, M, fl, &near);
       nn += near;
-      or_csweno_limit(m, a, fl, b, eps);
+      if (limit == 2) or_parent_weno_limit(m, a, fl, b, eps);
+      else or_csweno_limit(m, a, fl, b, eps);
       double* t = a; a = b; b = t;
     }
     if (pp) {
@@ -1402,10 +1450,17 @@ void or_project_ic(const or_mesh* m, int kind, const double* params, double* u) 
  * the invariants can be checked against what the oracle derived).
  * ----------------------------------------------------------------------------------*/
 int or_weno_tables_size(void) { return (int)sizeof(or_weno_tables); }
+/* parent: full-width stencil; ng_in > 0: reconstruction points r_in instead of Step 1's. */
+void or_weno_export_g(int N, int parent, int ng_in, const double* r_in, double* pt, double* wt, double* C, double* D,
+                      double* gam, double* B, double* SA, int* OFF, double* resid);
 void or_weno_export(int N, double* pt, double* wt, double* C, double* D, double* gam, double* B,
                     double* SA, int* OFF, double* resid) {
+  or_weno_export_g(N, 0, 0, NULL, pt, wt, C, D, gam, B, SA, OFF, resid);
+}
+void or_weno_export_g(int N, int parent, int ng_in, const double* r_in, double* pt, double* wt, double* C, double* D,
+                      double* gam, double* B, double* SA, int* OFF, double* resid) {
   or_weno_tables t;
-  or_weno_tables_build(N, &t);
+  weno_tables_build_g(N, parent, ng_in, r_in, &t);
   int ns = t.ns, ng = t.ng;
   for (int g = 0; g < ng; ++g) { pt[g] = t.pt[g]; wt[g] = t.wt[g]; }
   for (int i = 0; i <= N; ++i)
