@@ -332,6 +332,14 @@ def main():
             lmesh, ind_main, ms, clk, lim_learned, fallbacks, failures = mesh, dgl.IND_TVB, ms_plain, clk_plain, lim_plain, 0, 0
         value = aggregate_rate(dofs, args.steps, ms, world)
         value_plain = aggregate_rate(dofs, args.steps, ms_plain, world)
+        # the paper's own indicator (KXRCF) on the same workload, for comparison
+        kx = None
+        if args.arms == "both":
+            kmesh = make_mesh(False)
+            ms_kx, _, _, _, lim_kx = timed_arm(kmesh, dgl.IND_KXRCF, None)
+            kx = {"value": aggregate_rate(dofs, args.steps, ms_kx, world), "ms_per_step": ms_kx / args.steps,
+                  "limited_fraction": lim_kx}
+            kmesh.close()
 
         # ------------------------------------------------------------ dominant kernel alone
         mesh.set_modes(u0)
@@ -412,6 +420,7 @@ def main():
         "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps, "limited_fraction": lim_plain,
                   "tvb_flagged_fraction": tvb_frac},
         "learned_over_plain": value / value_plain,
+        "kxrcf": kx,
         "roofline": {"bound": "alu", "kernel": "k_stage2<Euler,P2>", "achieved": achieved, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                      "flops_per_cell": flops_cell, "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},
@@ -431,14 +440,30 @@ def main():
 
 def batched_arm(args, dist, rank, world, torch, dgl):
     """Batched workloads: many uneven instances in one mesh, per-instance time steps (CFL
-    0.1), plain TVB indicator, steps replayed from the CUDA graph."""
-    if args.workload == "burgers_batched":
-        w = W.burgers_2d_batched()
-    else:
-        w = W.euler_2d_batched()
+    0.1), steps replayed from the CUDA graph.  Burgers: the plain TVB indicator.  Euler P3:
+    the learned indicator (trained here on P3 four-quadrant problems, untimed) with its
+    plain-indicator fallback, next to the plain TVB arm; both with the positivity-preserving
+    scaling after every stage (random P3 four-quadrant problems lose positivity without it)."""
+    euler = args.workload != "burgers_batched"
+    w = W.euler_2d_batched() if euler else W.burgers_2d_batched()
     st = torch.cuda.Stream()
-    m = dgl.Mesh(2, w.pde, w.N, w.nx, w.ny, w.box, bc=w.bc, stream=st.cuda_stream)
-    m.project_ic(w.ic, w.params)
+    net, tau, tinfo, t_train = None, 0.0, {}, 0.0
+    if euler and args.arms == "both":
+        from paper_1904_11147_gb300 import train as T
+        t0 = time.perf_counter()
+        with torch.cuda.stream(st):
+            net, tau, tinfo = T.train_indicator(N=w.N, positivity=True, stream=st)
+        st.synchronize()
+        t_train = time.perf_counter() - t0
+
+    def make_mesh():
+        m = dgl.Mesh(2, w.pde, w.N, w.nx, w.ny, w.box, bc=w.bc, stream=st.cuda_stream)
+        m.project_ic(w.ic, w.params)
+        if euler:
+            m.set_positivity(True)
+        return m
+
+    m = make_mesh()
     ws = m.max_wavespeed()
     dts = []
     for i in range(w.n_inst):
@@ -448,37 +473,71 @@ def batched_arm(args, dist, rank, world, torch, dgl):
     m.set_dt(dts)
     tune = m.autotune(min(dts))
     m.set_dt(dts)
-    with torch.cuda.stream(st):
-        for _ in range(args.warmup):
-            m.step(0.0)
-        st.synchronize()
-        m.flag_statistics(reset=True)
-        barrier(dist)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = m.launches
-        with ClockSampler(args.clocks_out) as clk:
-            e0.record(st)
-            for _ in range(args.steps):
-                m.step(0.0)
-            e1.record(st)
-            e1.synchronize()
-        ms = max_over_ranks(dist, e0.elapsed_time(e1))
-        launches = m.launches - l0
-    tvbf, limited, passes = m.flag_statistics()
+    dofs = m.size
+
+    def timed(mm, ind, clk_path):
+        with torch.cuda.stream(st):
+            for _ in range(args.warmup):
+                mm.step(0.0, ind)
+            st.synchronize()
+            mm.flag_statistics(reset=True)
+            mm.positivity_counts(reset=True)
+            barrier(dist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = mm.launches
+            with ClockSampler(clk_path) as clk:
+                e0.record(st)
+                for _ in range(args.steps):
+                    mm.step(0.0, ind)
+                e1.record(st)
+                e1.synchronize()
+            ms_ = max_over_ranks(dist, e0.elapsed_time(e1))
+            launches_ = mm.launches - l0
+        tvbf, limited, passes = mm.flag_statistics()
+        # instances whose state is no longer finite (checked on the device, per instance)
+        u = torch.empty(dofs, dtype=torch.float64, device="cuda")
+        mm.get_modes(u)
+        per = dofs // w.cells
+        bad, off = 0, 0
+        for nx, ny in zip(w.nx, w.ny):
+            bad += not bool(torch.isfinite(u[off * per:(off + nx * ny) * per]).all())
+            off += nx * ny
+        del u
+        info = {"value": aggregate_rate(dofs, args.steps, ms_, world), "ms_per_step": ms_ / args.steps,
+                "limited_fraction": limited / max(passes, 1) / w.cells, "nonfinite_instances": int(bad)}
+        if euler:
+            info["positivity_scaled_cells"], info["inadmissible_means"] = mm.positivity_counts()
+        return ms_, launches_, clk, info
+
+    ms_plain, launches, clk_plain, plain = timed(m, dgl.IND_TVB, None if net is not None else args.clocks_out)
+    ms, info, clk = ms_plain, plain, clk_plain
+    if net is not None:
+        m.close()  # the full batch is ~20 GB per state copy: one mesh at a time
+        torch.cuda.synchronize()
+        lm = make_mesh()
+        lm.set_dt(dts)
+        lm.set_indicator(net, tau)
+        ms, launches, clk, info = timed(lm, dgl.IND_MLP, args.clocks_out)
+        info["positivity_fallbacks"], info["positivity_failures"] = lm.positivity_report()
+        info.update({"tau": tau, "train_s": t_train, "val_recall": tinfo.get("val_recall")})
     if rank != 0:
         return 0
-    dofs = m.size
-    value = dofs * args.steps * world / (ms / 1e3)
+    value = aggregate_rate(dofs, args.steps, ms, world)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "instances": w.n_inst, "cells": w.cells, "dofs": dofs, "indicator": "tvb",
+            "config": {"workload": w.name, "instances": w.n_inst, "cells": w.cells, "dofs": dofs,
+                       "indicator": "learned (TVB-gated MLP)" if net is not None else "tvb",
+                       "positivity_scaling": euler,
                        "limiter": "cswenolimit", "graph": True, "per_instance_dt": True,
                        "autotuned": {"stage_tile_rows": tune[0], "limiter_blocks_per_sm": tune[1],
-                                 "stage_persistent_queue": bool(tune[2])},
-                       "limited_fraction": limited / max(passes, 1) / w.cells,
+                                     "stage_persistent_queue": bool(tune[2])},
+                       "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "gpu_launches": launches, "clocks": clk.summary()}
+            "plain": plain, "gpu_launches": launches, "clocks": clk.summary()}
+    if net is not None:
+        line["learned"] = info
+        line["learned_over_plain"] = value / plain["value"]
     print(json.dumps(line))
     return 0
 

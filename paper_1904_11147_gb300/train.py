@@ -20,10 +20,11 @@ from . import BC_OUTFLOW, EULER, IND_TVB, MLP, Mesh, n_features
 from . import workloads as W
 
 
-def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, stream=None):
+def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, stream=None, positivity=False):
     """Runs the plain method on four-quadrant problems (one per seed) and returns device
     tensors X [S, F] (float32), TVB flags [S] (uint8) and the limiter's relative change [S]
-    (float32; zero for unflagged cells)."""
+    (float32; zero for unflagged cells).  positivity: apply the positivity-preserving
+    scaling after every stage's limiter (P3 runs lose positivity without it)."""
     st = stream or torch.cuda.current_stream()
     F = n_features(2, EULER, N)
     xs, fs, ls = [], [], []
@@ -51,6 +52,8 @@ def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, 
                     else:
                         m.flag_cells(IND_TVB, w.tvb_M)
                         m.cswenolimit()
+                    if positivity:
+                        m.positivity_limit()
                     k += 1
         st.synchronize()
         if not torch.isfinite(xs[-1]).all():
@@ -93,11 +96,11 @@ def choose_tau(net, X, y, recall=0.995):
 
 
 def train_indicator(seeds_train=(11, 12, 13, 14, 15, 16), seeds_val=(21, 22), n=96, steps=120, recall=0.995,
-                    epochs=6, seed=0, tol=0.05, stream=None):
-    """Harvest, train and calibrate a 2D Euler P2 indicator; returns (net, tau, info).
+                    epochs=6, seed=0, tol=0.05, stream=None, N=2, positivity=False):
+    """Harvest, train and calibrate a 2D Euler P^N indicator; returns (net, tau, info).
     Label: TVB-flagged and changed by the limiter by more than tol (relative to s_v)."""
-    Xt, ft, ct = harvest_quadrants(seeds_train, n=n, steps=steps, stream=stream)
-    Xv, fv, cv = harvest_quadrants(seeds_val, n=n, steps=steps, stream=stream)
+    Xt, ft, ct = harvest_quadrants(seeds_train, n=n, N=N, steps=steps, stream=stream, positivity=positivity)
+    Xv, fv, cv = harvest_quadrants(seeds_val, n=n, N=N, steps=steps, stream=stream, positivity=positivity)
     yt = (ct > tol).to(torch.uint8)
     yv = (cv > tol).to(torch.uint8)
     net = MLP(Xt.shape[1], seed=seed, stream=(stream or torch.cuda.current_stream()).cuda_stream)
