@@ -333,13 +333,20 @@ def main():
         value = aggregate_rate(dofs, args.steps, ms, world)
         value_plain = aggregate_rate(dofs, args.steps, ms_plain, world)
         # the paper's own indicator (KXRCF) on the same workload, for comparison
-        kx = None
+        kx = pw = None
         if args.arms == "both":
             kmesh = make_mesh(False)
             ms_kx, _, _, _, lim_kx = timed_arm(kmesh, dgl.IND_KXRCF, None)
             kx = {"value": aggregate_rate(dofs, args.steps, ms_kx, world), "ms_per_step": ms_kx / args.steps,
                   "limited_fraction": lim_kx}
             kmesh.close()
+            # the parent WENO limiter (full-width stencil) on the TVB flags, for comparison
+            pmesh = make_mesh(False)
+            pmesh.set_limiter(dgl.LIM_PARENT)
+            ms_pw, _, _, _, lim_pw = timed_arm(pmesh, dgl.IND_TVB, None)
+            pw = {"value": aggregate_rate(dofs, args.steps, ms_pw, world), "ms_per_step": ms_pw / args.steps,
+                  "limited_fraction": lim_pw}
+            pmesh.close()
 
         # ------------------------------------------------------------ dominant kernel alone
         mesh.set_modes(u0)
@@ -421,6 +428,7 @@ def main():
                   "tvb_flagged_fraction": tvb_frac},
         "learned_over_plain": value / value_plain,
         "kxrcf": kx,
+        "parent_weno": pw,
         "roofline": {"bound": "alu", "kernel": "k_stage2<Euler,P2>", "achieved": achieved, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
                      "flops_per_cell": flops_cell, "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},

@@ -48,6 +48,7 @@ typedef enum {
 typedef enum { DG_BURGERS = 0, DG_EULER = 1 } dg_pde;
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 } dg_bc;
 typedef enum { DG_IND_TVB = 0, DG_IND_MLP = 1, DG_IND_KXRCF = 2 } dg_indicator;
+typedef enum { DG_LIM_CSWENO = 0, DG_LIM_PARENT = 1 } dg_limiter;
 
 /* Initial-condition families for dg_project_ic (parameters per instance):
  *   DG_IC_SINE          u = p0 + p1 sin(p2 x + p3 y)                              (4)
@@ -125,6 +126,20 @@ dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flag
  * fields for Euler; dimension by dimension in 2D).  Jacobi update: every troubled cell
  * reads the unlimited neighbours.  Errors: DG_ESTATE if no flags exist for this state. */
 dg_status dg_cswenolimit(dg_mesh* m);
+
+/* The parent WENO limiter (Qiu and Shu, ref. [qs1]; the limiter Sec. 4 compares CSWENO
+ * with) on the cells flagged by the last dg_flag_cells: the reconstruction of Sec. 3,
+ * Steps 2-6, on the averages of the whole cells j-N..j+N (in 2D the (2N+1)^2 cell averages
+ * around the troubled cell, x sweep then y sweep; characteristic fields for Euler).
+ * Outflow ghosts mirror the interior cell at the reflected position.  Jacobi update, U_0
+ * kept.  Errors: DG_ESTATE (no flags for this state), DG_EINVAL (an instance with fewer
+ * than N+1 cells per side). */
+dg_status dg_parent_wenolimit(dg_mesh* m);
+
+/* Limiter used by dg_step with the TVB and KXRCF indicators: DG_LIM_CSWENO (default) or
+ * DG_LIM_PARENT (the learned indicator always uses CSWENO).  The CUDA graph is rebuilt on
+ * the next dg_step.  Errors: DG_EINVAL (unknown limiter, instance too small). */
+dg_status dg_set_limiter(dg_mesh* m, int limiter);
 
 /* Positivity-preserving scaling (Example 11 adds it to the limiter, following Zhang and
  * Shu, ref. [zs3]) of the current state, every cell, Euler only.  For a cell whose mean

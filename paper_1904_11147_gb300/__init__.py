@@ -19,6 +19,7 @@ DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EPOSITIVITY, DG_ETIMEOUT, DG_ESTATE = 
 BURGERS, EULER = 0, 1
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 IND_TVB, IND_MLP, IND_KXRCF = 0, 1, 2
+LIM_CSWENO, LIM_PARENT = 0, 1
 IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
 STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EPOSITIVITY",
                 5: "DG_ETIMEOUT", 6: "DG_ESTATE"}
@@ -85,6 +86,8 @@ def lib():
             l.dg_indicator_logits.argtypes = [P, P]
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             l.dg_positivity_limit.argtypes = [P, ctypes.c_double]
+            l.dg_parent_wenolimit.argtypes = [P]
+            l.dg_set_limiter.argtypes = [P, ctypes.c_int]
             l.dg_set_positivity.argtypes = [P, ctypes.c_int, ctypes.c_double]
             l.dg_positivity_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                                ctypes.c_int]
@@ -93,7 +96,8 @@ def lib():
                          "dg_max_wavespeed", "dg_limiter_tables", "dg_mlp_create", "dg_mlp_destroy",
                          "dg_mlp_get_params", "dg_mlp_set_params", "dg_mlp_grad", "dg_mlp_train_step",
                          "dg_set_indicator_mlp", "dg_indicator_logits", "dg_harvest", "dg_mlp_predict",
-                         "dg_positivity_limit", "dg_set_positivity", "dg_positivity_counts"):
+                         "dg_positivity_limit", "dg_set_positivity", "dg_positivity_counts",
+                         "dg_parent_wenolimit", "dg_set_limiter"):
                 getattr(l, name).restype = ctypes.c_int
             _lib = l
     return _lib
@@ -212,6 +216,14 @@ class Mesh:
 
     def step(self, dt, indicator=IND_TVB, M=0.01):
         _check(lib().dg_step(self._h, dt, indicator, M))
+
+    def parent_wenolimit(self):
+        """Parent WENO limiter on the flagged cells (see dg_parent_wenolimit)."""
+        _check(lib().dg_parent_wenolimit(self._h))
+
+    def set_limiter(self, limiter):
+        """Limiter of step() with the TVB / KXRCF indicators: LIM_CSWENO or LIM_PARENT."""
+        _check(lib().dg_set_limiter(self._h, int(limiter)))
 
     def positivity_limit(self, eps0=1e-13):
         """Positivity-preserving scaling of the current state (see dg_positivity_limit)."""

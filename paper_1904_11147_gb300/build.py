@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcswenodg.so")
 SOURCES = ["dg_kernels2d.cu", "dg_kernels1d.cu", "dg_mlp.cu", "dg_api.cu", "dg_noalloc.cu", "dg_positivity.cu",
-           "dg_kxrcf.cu", "tables.cpp"]
+           "dg_kxrcf.cu", "dg_parent.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -71,6 +71,9 @@ void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* p
                             double gam, const int* lc, const int* li, const Counters* cnt, const unsigned char* flags,
                             int skip_kept, unsigned int* fail, int nblocks);
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total);
+cudaError_t upload_tables_parent(const dgt::Tabs* tabs);
+void launch_parent(int dim, int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
+                   double* lim, int nblocks);
 void launch_kxrcf(int dim, int pde, int N, const LaunchArgs& a, const double* hpow, const double* psi_m1,
                   const double* psi_p1, const double* psi_q, const double* gw, unsigned char* flags, Counters* cnt,
                   int* lc, int* li);
@@ -105,13 +108,15 @@ void dg_set_error_internal(const char* msg) { snprintf(g_err, sizeof(g_err), "%s
 // ----------------------------------------------------------------------------- tables
 static int g_tables_dev = -2;  // device the constant tables were uploaded to (per process)
 static dgt::Tabs g_tabs[3];
+static dgt::Tabs g_ptabs[3];  // parent WENO limiter tables (full-width stencil)
 
 dg_status dg_ensure_tables_internal() {
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (g_tables_dev == -2) {
     for (int n = 1; n <= 3; ++n)
-      if (dgt::build_tables(n, &g_tabs[n - 1])) return fail(DG_EINVAL, "table derivation failed for N=%d", n);
+      if (dgt::build_tables(n, &g_tabs[n - 1]) || dgt::build_tables(n, &g_ptabs[n - 1], true))
+        return fail(DG_EINVAL, "table derivation failed for N=%d", n);
   }
   // constant memory is per device: upload once for every device that creates a mesh
   static std::vector<int> done;
@@ -119,6 +124,7 @@ dg_status dg_ensure_tables_internal() {
     if (d == dev) return DG_OK;
   CK(upload_tables1(g_tabs));
   CK(upload_tables2(g_tabs));
+  CK(upload_tables_parent(g_ptabs));
   done.push_back(dev);
   g_tables_dev = dev;
   return DG_OK;
@@ -187,6 +193,10 @@ struct dg_mesh {
   // values at r = -1, +1 and at the Gauss points, with the Gauss weights
   double* d_kx_hpow = nullptr;
   double kx_pm[4], kx_pp[4], kx_pq[16], kx_w[4];
+  // limiter of dg_step with the TVB / KXRCF indicators: CSWENO (default) or parent WENO
+  int limiter = DG_LIM_CSWENO;
+  int g_lim = -1;
+  int min_side = 1;  // smallest instance side (the parent stencil needs N+1 cells)
 };
 
 static size_t mesh_doubles(const dg_mesh* m) { return (size_t)m->ncell * m->V * m->NP; }
@@ -333,6 +343,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   }
   m->ncell = off;
   m->ctot = (off + 31) / 32 * 32;
+  m->min_side = 1 << 30;
+  for (const Inst& I : m->h_inst) m->min_side = std::min(m->min_side, dim == 1 ? I.nx : std::min(I.nx, I.ny));
   m->ntiles = (int)tiles.size();
   m->last_dt.assign(n_inst, 0.0);
   std::vector<int> cell_inst(off);
@@ -527,6 +539,14 @@ static void k_flag(dg_mesh* m, double M) {
   m->launches++;
 }
 
+static void k_parent_list(dg_mesh* m, const int* lc, const int* li, const Counters* cnt) {
+  auto a = args<LaunchArgs>(m, 0, m->cur, m->cur);
+  launch_parent(m->dim, m->pde, m->N, a, lc, li, cnt, m->lim, m->limit_blocks);
+  if (m->dim == 1) launch_scatter1(m->pde, m->N, a, m->lim, lc, cnt, m->limit_blocks);
+  else launch_scatter2(m->pde, m->N, a, m->lim, lc, cnt, m->limit_blocks);
+  m->launches += 2;
+}
+
 static void k_limit_list(dg_mesh* m, const int* lc, const int* li, const Counters* cnt) {
   auto a = args<LaunchArgs>(m, 0, m->cur, m->cur);
   if (m->dim == 1) {
@@ -715,6 +735,26 @@ extern "C" dg_status dg_cswenolimit(dg_mesh* m) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_parent_wenolimit(dg_mesh* m) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (!m->flags_valid) return fail(DG_ESTATE, "no troubled-cell flags for the current state");
+  if (m->min_side < m->N + 1) return fail(DG_EINVAL, "the parent WENO stencil needs %d cells per side", m->N + 1);
+  if (m->use_b) k_parent_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
+  else k_parent_list(m, m->list_cell, m->list_inst, m->cnt);
+  CK(cudaGetLastError());
+  m->flags_valid = false;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_limiter(dg_mesh* m, int limiter) {
+  if (!m) return fail(DG_EINVAL, "null mesh");
+  if (limiter != DG_LIM_CSWENO && limiter != DG_LIM_PARENT) return fail(DG_EINVAL, "unknown limiter %d", limiter);
+  if (limiter == DG_LIM_PARENT && m->min_side < m->N + 1)
+    return fail(DG_EINVAL, "the parent WENO stencil needs %d cells per side", m->N + 1);
+  m->limiter = limiter;
+  return DG_OK;
+}
+
 extern "C" dg_status dg_positivity_limit(dg_mesh* m, double eps0) {
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (m->pde != DG_EULER) return fail(DG_EINVAL, "the positivity-preserving scaling is defined for the Euler equations");
@@ -771,7 +811,8 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
       CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
       if (indicator == DG_IND_KXRCF) k_flag_kx(m);
       else k_flag(m, M);
-      k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
+      if (m->limiter == DG_LIM_PARENT) k_parent_list(m, m->list_cell, m->list_inst, m->cnt);
+      else k_limit_list(m, m->list_cell, m->list_inst, m->cnt);
       k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt, nullptr, m->flag_totals);
     }
     m->launches++;
@@ -807,7 +848,8 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
     m->flags_valid = false;
     return s;
   }
-  if (!m->gexec || m->g_ind != indicator || m->g_M != tvb_M || m->g_pp != m->pp_on || m->g_pp_eps != m->pp_eps0) {
+  if (!m->gexec || m->g_ind != indicator || m->g_M != tvb_M || m->g_pp != m->pp_on || m->g_pp_eps != m->pp_eps0 ||
+      m->g_lim != m->limiter) {
     if (m->gexec) {
       cudaGraphExecDestroy(m->gexec);
       m->gexec = nullptr;
@@ -828,6 +870,7 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
     m->g_M = tvb_M;
     m->g_pp = m->pp_on;
     m->g_pp_eps = m->pp_eps0;
+    m->g_lim = m->limiter;
   }
   CK(cudaGraphLaunch(m->gexec, m->st));
   m->launches += m->g_kernels;

@@ -11,9 +11,12 @@
 // direction); face integrals use the (N+1)-point Gauss rule along the face.  Neighbours
 // follow the boundary condition (periodic, or the mirrored boundary cell at outflow).
 //
-// Every sum is written with explicit round-to-nearest operations in a fixed order (no
-// contraction into FMAs), so the decision is a fixed sequence of IEEE-754 operations on
-// the modes and the basis values.  One thread per cell on the tiles of the TVB indicator.
+// A face trace has degree N along the face and the (N+1)-point Gauss rule integrates it
+// exactly, so by orthonormality the face integral keeps only the transverse-degree-0
+// part: int_face w ds = |face| / sqrt(2) * sum_a U_a0 psi_a(+-1).  The Gauss-point maximum
+// uses sum factorisation.  This is the oracle's definition evaluated in fewer operations:
+// the decisions agree except where num and den are within rounding of each other (the
+// near-threshold cells, counted).  One thread per cell on the tiles of the TVB indicator.
 #include "dg_shared.cuh"
 
 namespace dg {
@@ -74,6 +77,7 @@ __global__ void __launch_bounds__(256) k_kxrcf(const double* __restrict__ U, con
       }
       return I.off + (long long)jy * I.nx + jx;
     };
+    constexpr double kInvSqrt2 = 0.70710678118654752440;
 #pragma unroll
     for (int iw = 0; iw < NW; ++iw) {
       const int v = iw == 0 ? 0 : V - 1;
@@ -87,69 +91,54 @@ __global__ void __launch_bounds__(256) k_kxrcf(const double* __restrict__ U, con
         if (!in[f]) continue;
         bool mirror;
         const long long gn = neighbour(f, mirror);
-        double un[NP];
+        // own trace at the face (normal degree n, transverse degree 0) and the
+        // neighbour's trace at the same face (its opposite side)
+        const bool low = (f & 1) == 0;  // W or S face: own side r = -1, neighbour's r = +1
+        double a = 0.0, b = 0.0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          const int a = DIM == 1 ? k : mode_a(k), b = DIM == 1 ? 0 : mode_b(k);
-          const bool odd = f < 2 ? (a & 1) : (b & 1);
+        for (int n = 0; n <= N; ++n) {
+          const int k = DIM == 1 ? n : (f < 2 ? mode_idx(n, 0) : mode_idx(0, n));
           const double x = P[(long long)k * ctot + gn];
-          un[k] = (mirror && odd) ? -x : x;
+          const double xn = (mirror && (n & 1)) ? -x : x;
+          a = fma(uc[k], low ? tb.pm[n] : tb.pp[n], a);
+          b = fma(xn, low ? tb.pp[n] : tb.pm[n], b);
         }
-        if (DIM == 1) {
-          double a = 0.0, b = 0.0;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) {
-            a = __dadd_rn(a, __dmul_rn(uc[k], f == 0 ? tb.pm[k] : tb.pp[k]));
-            b = __dadd_rn(b, __dmul_rn(un[k], f == 0 ? tb.pp[k] : tb.pm[k]));
-          }
-          num = __dadd_rn(num, __dsub_rn(a, b));
-          len = __dadd_rn(len, 1.0);
-        } else {
-          double s = 0.0;
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            double a = 0.0, b = 0.0;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-              const int ka = mode_a(k), kb = mode_b(k);
-              double po, pn;
-              if (f == 0) { po = __dmul_rn(tb.pm[ka], tb.pq[q][kb]); pn = __dmul_rn(tb.pp[ka], tb.pq[q][kb]); }
-              else if (f == 1) { po = __dmul_rn(tb.pp[ka], tb.pq[q][kb]); pn = __dmul_rn(tb.pm[ka], tb.pq[q][kb]); }
-              else if (f == 2) { po = __dmul_rn(tb.pq[q][ka], tb.pm[kb]); pn = __dmul_rn(tb.pq[q][ka], tb.pp[kb]); }
-              else { po = __dmul_rn(tb.pq[q][ka], tb.pp[kb]); pn = __dmul_rn(tb.pq[q][ka], tb.pm[kb]); }
-              a = __dadd_rn(a, __dmul_rn(uc[k], po));
-              b = __dadd_rn(b, __dmul_rn(un[k], pn));
-            }
-            s = __dadd_rn(s, __dmul_rn(tb.w[q], __dsub_rn(a, b)));
-          }
-          const double flen = f < 2 ? I.hy : I.hx;
-          num = __dadd_rn(num, __dmul_rn(s, __dmul_rn(0.5, flen)));
-          len = __dadd_rn(len, flen);
-        }
+        const double flen = DIM == 1 ? 1.0 : (f < 2 ? I.hy : I.hx);
+        num = fma(flen, a - b, num);
+        len += flen;
       }
       if (len == 0.0) continue;
+      if (DIM == 2) num *= kInvSqrt2;
       double nrm = 0.0;
       if (DIM == 1) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           double a = 0.0;
 #pragma unroll
-          for (int k = 0; k < NP; ++k) a = __dadd_rn(a, __dmul_rn(uc[k], tb.pq[q][k]));
-          if (fabs(a) > nrm) nrm = fabs(a);
+          for (int k = 0; k < NP; ++k) a = fma(uc[k], tb.pq[q][k], a);
+          nrm = fmax(nrm, fabs(a));
         }
       } else {
 #pragma unroll
-        for (int qx = 0; qx < Q; ++qx)
+        for (int qx = 0; qx < Q; ++qx) {
+          double t[N + 1];
+#pragma unroll
+          for (int b = 0; b <= N; ++b) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a <= N - b; ++a) s = fma(uc[mode_idx(a, b)], tb.pq[qx][a], s);
+            t[b] = s;
+          }
 #pragma unroll
           for (int qy = 0; qy < Q; ++qy) {
-            double a = 0.0;
+            double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < NP; ++k)
-              a = __dadd_rn(a, __dmul_rn(uc[k], __dmul_rn(tb.pq[qx][mode_a(k)], tb.pq[qy][mode_b(k)])));
-            if (fabs(a) > nrm) nrm = fabs(a);
+            for (int b = 0; b <= N; ++b) s = fma(t[b], tb.pq[qy][b], s);
+            nrm = fmax(nrm, fabs(s));
           }
+        }
       }
-      const double den = __dmul_rn(__dmul_rn(hp, len), nrm), an = fabs(num);
+      const double den = hp * len * nrm, an = fabs(num);
       if (kx_near(an, den)) near = true;
       if (an > den) fl = 1;
     }

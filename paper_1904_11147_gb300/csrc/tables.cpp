@@ -133,7 +133,7 @@ void primitive_deriv_rows(int n, const ld* e, int l, ld x, ld* w) {
 
 }  // namespace
 
-int build_tables(int N, Tabs* t) {
+int build_tables(int N, Tabs* t, bool parent) {
   if (N < 1 || N > kMaxN) return 1;
   std::memset(t, 0, sizeof(*t));
   t->N = N;
@@ -181,13 +181,19 @@ int build_tables(int N, Tabs* t) {
     t->rw[g] = (double)rw[g];
     for (int n = 0; n <= N; ++n) t->psiG[g][n] = (double)psi(n, rp[g]);
   }
-  // stencil edges, in units of the troubled cell's width (troubled cell = [-1/2, 1/2])
+  // stencil edges, in units of the troubled cell's width (troubled cell = [-1/2, 1/2]):
+  // CSWENO splits the immediate neighbours into N parts; the parent WENO limiter (Qiu and
+  // Shu) uses the whole cells j-N .. j+N
   int ns = t->NS;
   ld e[kMaxS + 1];
-  for (int k = 0; k <= N; ++k) e[k] = -1.5L + (ld)k / N;
-  for (int k = 1; k <= N; ++k) e[N + k] = 0.5L + (ld)(k - 1) / N;
-  e[2 * N + 1] = 1.5L;
-  // (the loop above sets e[N+1] = 0.5, the troubled cell's right edge)
+  if (parent) {
+    for (int k = 0; k <= ns; ++k) e[k] = -(ld)N - 0.5L + k;
+  } else {
+    for (int k = 0; k <= N; ++k) e[k] = -1.5L + (ld)k / N;
+    for (int k = 1; k <= N; ++k) e[N + k] = 0.5L + (ld)(k - 1) / N;
+    e[2 * N + 1] = 1.5L;
+    // (the loop above sets e[N+1] = 0.5, the troubled cell's right edge)
+  }
   for (int g = 0; g < t->NG; ++g) {
     ld xi = rp[g] / 2;
     ld Cl[kMaxN + 1][kMaxN + 1];
@@ -259,6 +265,12 @@ int build_tables(int N, Tabs* t) {
     gauss(6, qx, qw);
     for (int k = 0; k < ns; ++k) {
       ld a, b;
+      if (parent) {  // whole cell j + k - N: only its mean enters
+        t->OFF[k] = k - N;
+        t->SA[k][0] = (double)psi(0, 0.0L);
+        for (int n = 1; n <= N; ++n) t->SA[k][n] = 0.0;
+        continue;
+      }
       if (k < N) { a = -1 + 2.0L * k / N; b = -1 + 2.0L * (k + 1) / N; t->OFF[k] = -1; }
       else if (k == N) { a = -1; b = 1; t->OFF[k] = 0; }
       else { int q = k - N - 1; a = -1 + 2.0L * q / N; b = -1 + 2.0L * (q + 1) / N; t->OFF[k] = 1; }

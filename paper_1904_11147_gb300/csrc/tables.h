@@ -35,7 +35,8 @@ struct Tabs {
   double gam_resid;                          // residual of the full Eq. (8) system
 };
 
-// Fills t for degree N; returns 0 on success.
-int build_tables(int N, Tabs* t);
+// Fills t for degree N; returns 0 on success.  parent: the limiter tables of the parent
+// WENO limiter (whole cells j-N .. j+N) instead of CSWENO's subcells.
+int build_tables(int N, Tabs* t, bool parent = false);
 
 }  // namespace dgt

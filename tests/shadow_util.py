@@ -23,15 +23,17 @@ def rel(a, b):
 
 
 def shadow_stages(o, g, u0, dt, steps, M=0.01, pp_eps=None, graph_check=True, stop_on_nonfinite=False, t_end=None,
-                  indicator="tvb"):
+                  indicator="tvb", limiter="csweno"):
     """dt: a number or a function of (step, state).  With t_end the last step is cut to
     end there.  stop_on_nonfinite: a stage output that is not finite on both sides ends
     the run (it must be non-finite on both).  indicator: "tvb" (flags identical) or
     "kxrcf" (flags identical up to the oracle's near-threshold cells: the two sides'
     basis values at the Gauss points are derived independently and may differ in the last
     bit).  Returns (worst stage deviation, worst limited deviation, flagged cells in
-    total, steps done, time reached)."""
+    total, steps done, time reached).  limiter: "csweno" or "parent" (parent WENO)."""
     ind = dgl.IND_KXRCF if indicator == "kxrcf" else dgl.IND_TVB
+    parent = limiter == "parent"
+    g.set_limiter(dgl.LIM_PARENT if parent else dgl.LIM_CSWENO)
     g.set_modes(u0)
     if pp_eps is not None:
         g.set_positivity(True, pp_eps)
@@ -65,9 +67,12 @@ def shadow_stages(o, g, u0, dt, steps, M=0.01, pp_eps=None, graph_check=True, st
                 fl_o, nf_o, _ = o.flag_tvb(got, M)
                 assert nf == nf_o and np.array_equal(fl_g, fl_o), (k, s, "flags", int((fl_g != fl_o).sum()))
             flagged += nf
-            g.cswenolimit()
+            if parent:
+                g.parent_wenolimit()
+            else:
+                g.cswenolimit()
             lim = g.get_modes()
-            d = rel(lim, o.limit(got, fl_g))
+            d = rel(lim, o.parent_limit(got, fl_g) if parent else o.limit(got, fl_g))
             assert d <= 1e-11, (k, s, "limiter", d)
             worst_lim = max(worst_lim, d)
             if pp_eps is not None:
