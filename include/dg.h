@@ -55,8 +55,21 @@ typedef enum { DG_LIM_CSWENO = 0, DG_LIM_PARENT = 1 } dg_limiter;
  *   DG_IC_RIEMANN1D     (rho,u,p) = p0..p2 for x < p6, p3..p5 otherwise           (7)
  *   DG_IC_QUADRANT      (rho,u,v,p) for x>=p16,y>=p17: p0..3; x<p16,y>=p17: p4..7;
  *                       x<p16,y<p17: p8..11; x>=p16,y<p17: p12..15                 (18)
- *   DG_IC_DENSITY_WAVE  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6     (7) */
-typedef enum { DG_IC_SINE = 0, DG_IC_RIEMANN1D = 1, DG_IC_QUADRANT = 2, DG_IC_DENSITY_WAVE = 3 } dg_ic;
+ *   DG_IC_DENSITY_WAVE  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6     (7)
+ *   DG_IC_SHOCK_ENTROPY (1D, Example 9) (rho,u,p) = p0..p2 for x < p3, otherwise
+ *                       rho = p4 + p5 sin(p6 x), u = p7, p = p8                     (9)
+ *   DG_IC_VORTEX        (2D, Example 4) isentropic vortex centred at (p0 + p3, p1),
+ *                       strength p2, at time p3: rho = (1 - (g-1) p2^2 e^{2(1-r^2)} /
+ *                       (16 g pi^2))^{1/(g-1)}, u = 1 - p2 e^{1-r^2} (y-p1)/(2 pi),
+ *                       v = p2 e^{1-r^2} (x-p0-p3)/(2 pi), p = rho^g               (4) */
+typedef enum {
+  DG_IC_SINE = 0,
+  DG_IC_RIEMANN1D = 1,
+  DG_IC_QUADRANT = 2,
+  DG_IC_DENSITY_WAVE = 3,
+  DG_IC_SHOCK_ENTROPY = 4,
+  DG_IC_VORTEX = 5
+} dg_ic;
 
 /* Create a batch of n_inst meshes sharing dim, PDE, order N and boundary condition.
  *  dim      1 or 2.  pde: dg_pde.  N: polynomial degree 1..3 (Sec. 2, P^N).

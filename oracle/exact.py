@@ -109,6 +109,17 @@ def riemann_exact(WL, WR, gamma, xi):
     return rho, u, pr, (ps, us)
 
 
+def vortex_exact(x, y, t, x0=5.0, y0=0.0, beta=5.0, gamma=1.4):
+    """Example 4's printed exact solution: the isentropic vortex advected with speed 1 in
+    x; returns (rho, u, v, p) at the points (x, y) and time t."""
+    dx, dy = x - x0 - t, y - y0
+    e = np.exp(1.0 - (dx * dx + dy * dy))
+    rho = (1.0 - (gamma - 1.0) * beta ** 2 * e * e / (16.0 * gamma * np.pi ** 2)) ** (1.0 / (gamma - 1.0))
+    u = 1.0 - beta * e * dy / (2.0 * np.pi)
+    v = beta * e * dx / (2.0 * np.pi)
+    return rho, u, v, rho ** gamma
+
+
 def eval_points(mesh, u, nq):
     """Values of the modal solution at nq Gauss points per direction per cell.
 

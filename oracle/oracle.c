@@ -1390,6 +1390,10 @@ void or_max_wavespeed(const or_mesh* m, const double* u, double* out) {
  *   2 four quadrants (2D Euler): (rho,u,v,p) for x>=p16,y>=p17 (p0..3), x<p16,y>=p17
  *     (p4..7), x<p16,y<p17 (p8..11), x>=p16,y<p17 (p12..15)
  *   3 density wave (Euler): rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6
+ *   4 shock/entropy wave (1D Euler, Example 9): (rho,u,p) = p0..p2 for x < p3, else
+ *     rho = p4 + p5 sin(p6 x), u = p7, p = p8
+ *   5 isentropic vortex (2D Euler, Example 4): the printed exact solution with centre
+ *     (p0, p1), strength beta = p2, evaluated at time p3 (advected with speed 1 in x)
  * ----------------------------------------------------------------------------------*/
 static void ic_eval(int dim, int pde, double gam, int kind, const double* p, double x, double y, double* u) {
   if (kind == 0) { u[0] = p[0] + p[1] * sin(p[2] * x + p[3] * y); return; }
@@ -1400,6 +1404,19 @@ static void ic_eval(int dim, int pde, double gam, int kind, const double* p, dou
   } else if (kind == 2) {
     int q = (x >= p[16]) ? (y >= p[17] ? 0 : 3) : (y >= p[17] ? 1 : 2);
     rho = p[4 * q]; vx = p[4 * q + 1]; vy = p[4 * q + 2]; pr = p[4 * q + 3];
+  } else if (kind == 4) { /* Example 9: a shock running into an entropy (density) wave */
+    int left = x < p[3];
+    rho = left ? p[0] : p[4] + p[5] * sin(p[6] * x);
+    vx = left ? p[1] : p[7];
+    pr = left ? p[2] : p[8];
+  } else if (kind == 5) { /* Example 4: isentropic vortex (exact solution at time p3) */
+    const double pi = 3.14159265358979323846;
+    double dx = x - p[0] - p[3], dy = y - p[1];
+    double e = exp(1.0 - (dx * dx + dy * dy));
+    rho = pow(1.0 - (gam - 1.0) * p[2] * p[2] * e * e / (16.0 * gam * pi * pi), 1.0 / (gam - 1.0));
+    vx = 1.0 - p[2] * e * dy / (2.0 * pi);
+    vy = p[2] * e * dx / (2.0 * pi);
+    pr = pow(rho, gam);
   } else {
     rho = p[0] + p[1] * sin(p[2] * x + p[3] * y); vx = p[4]; vy = p[5]; pr = p[6];
   }

@@ -636,12 +636,13 @@ extern "C" dg_status dg_get_modes(dg_mesh* m, double* out, size_t n, int is_devi
 
 extern "C" dg_status dg_project_ic(dg_mesh* m, int ic, const double* params, int nparams) {
   if (!m || !params) return fail(DG_EINVAL, "null argument");
-  static const int need[4] = {4, 7, 18, 7};
-  if (ic < 0 || ic > 3) return fail(DG_EINVAL, "unknown initial condition %d", ic);
+  static const int need[6] = {4, 7, 18, 7, 9, 4};
+  if (ic < 0 || ic > 5) return fail(DG_EINVAL, "unknown initial condition %d", ic);
   if (nparams < need[ic]) return fail(DG_EINVAL, "initial condition %d needs %d parameters", ic, need[ic]);
   if ((m->pde == DG_BURGERS) != (ic == DG_IC_SINE)) return fail(DG_EINVAL, "initial condition does not fit the PDE");
-  if (ic == DG_IC_RIEMANN1D && m->dim != 1) return fail(DG_EINVAL, "1D Riemann data on a 2D mesh");
-  if (ic == DG_IC_QUADRANT && m->dim != 2) return fail(DG_EINVAL, "quadrant data on a 1D mesh");
+  if ((ic == DG_IC_RIEMANN1D || ic == DG_IC_SHOCK_ENTROPY) && m->dim != 1)
+    return fail(DG_EINVAL, "1D initial data on a 2D mesh");
+  if ((ic == DG_IC_QUADRANT || ic == DG_IC_VORTEX) && m->dim != 2) return fail(DG_EINVAL, "2D initial data on a 1D mesh");
   // parameters go through the limiter scratch buffer (large enough for any batch)
   const size_t bytes = sizeof(double) * (size_t)m->n_inst * nparams;
   if (bytes > (size_t)m->ctot * m->V * m->NP * sizeof(double)) return fail(DG_EINVAL, "too many parameters");

@@ -1,6 +1,7 @@
 // 1D kernels (P^N, N = 1..3; Burgers V = 1, Euler V = 3).  The 1D workloads are small
 // (hundreds to thousands of cells), so these kernels favour simplicity: one thread per
 // cell, the two face fluxes of a cell evaluated by that cell.
+#include "dg_ic.cuh"
 #include "dg_shared.cuh"
 #include "tables.h"
 
@@ -364,17 +365,6 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-__device__ __forceinline__ void ic_eval1(int kind, const double* p, double x, double gam, double* u) {
-  if (kind == 0) { u[0] = p[0] + p[1] * sin(p[2] * x); return; }
-  double rho, vel, pr;
-  if (kind == 1) {
-    const bool left = x < p[6];
-    rho = left ? p[0] : p[3]; vel = left ? p[1] : p[4]; pr = left ? p[2] : p[5];
-  } else {
-    rho = p[0] + p[1] * sin(p[2] * x); vel = p[4]; pr = p[6];
-  }
-  u[0] = rho; u[1] = rho * vel; u[2] = pr / (gam - 1.0) + 0.5 * rho * vel * vel;
-}
 
 template <int PDE, int N>
 __global__ void k_project1(double* __restrict__ U, const Inst* __restrict__ insts, const int* __restrict__ cell_inst,

@@ -11,6 +11,7 @@
 // FP64 arithmetic is the bound on GB300 (the FP64 pipe runs at 1/64 of FP32), so the
 // kernels are laid out to keep every lane of every FP64 warp instruction useful and to
 // avoid recomputing traces or face fluxes.
+#include "dg_ic.cuh"
 #include "dg_shared.cuh"
 #include "tables.h"
 
@@ -961,19 +962,6 @@ __global__ void __launch_bounds__(128)
 // ----------------------------------------------------------------------------- projection
 // Eq. (2) for the initial data: U_ab = sum_{qx,qy} w w u0(x, y) psi_a psi_b with N+4 Gauss
 // points per direction.  Parameters per instance (see dg.h for the families).
-__device__ __forceinline__ void ic_eval2(int kind, const double* p, double x, double y, double gam, int pde,
-                                         double* u) {
-  if (kind == 0) { u[0] = p[0] + p[1] * sin(p[2] * x + p[3] * y); return; }
-  double rho, vx, vy, pr;
-  if (kind == 2) {
-    const int q = (x >= p[16]) ? (y >= p[17] ? 0 : 3) : (y >= p[17] ? 1 : 2);
-    rho = p[4 * q]; vx = p[4 * q + 1]; vy = p[4 * q + 2]; pr = p[4 * q + 3];
-  } else {  // density wave
-    rho = p[0] + p[1] * sin(p[2] * x + p[3] * y); vx = p[4]; vy = p[5]; pr = p[6];
-  }
-  u[0] = rho; u[1] = rho * vx; u[2] = rho * vy; u[3] = pr / (gam - 1.0) + 0.5 * rho * (vx * vx + vy * vy);
-  (void)pde;
-}
 
 template <int PDE, int N>
 __global__ void k_project2(double* __restrict__ U, const Inst* __restrict__ insts, const int* __restrict__ cell_inst,
@@ -998,7 +986,7 @@ __global__ void k_project2(double* __restrict__ U, const Inst* __restrict__ inst
       const double x = I.xL + I.hx * (ix + 0.5 * (1.0 + T(O::PX + qx)));
       const double y = I.yL + I.hy * (iy + 0.5 * (1.0 + T(O::PX + qy)));
       double u[V];
-      ic_eval2(kind, p, x, y, gam, PDE, u);
+      ic_eval2(kind, p, x, y, gam, u);
       const double ww = T(O::PW + qx) * T(O::PW + qy);
 #pragma unroll
       for (int m = 0; m < NP; ++m) {

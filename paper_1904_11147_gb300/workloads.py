@@ -12,6 +12,8 @@ Initial-condition families (``ic`` codes shared with the library's projection ca
   2 four quadrant: (rho,u,v,p) for x>=p16,y>=p17 (p0..3); x<p16,y>=p17 (p4..7);
                    x<p16,y<p17 (p8..11); x>=p16,y<p17 (p12..15)
   3 density wave:  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6
+  4 shock/entropy: (rho,u,p) = p0..p2 for x < p3, else rho = p4 + p5 sin(p6 x), u = p7, p = p8
+  5 vortex:        isentropic vortex centred at (p0 + p3, p1), strength p2, at time p3
 """
 from __future__ import annotations
 
@@ -24,7 +26,7 @@ SEED = 1904
 
 PDE_BURGERS, PDE_EULER = 0, 1
 BC_PERIODIC, BC_OUTFLOW = 0, 1
-IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE, IC_SHOCK_ENTROPY, IC_VORTEX = 0, 1, 2, 3, 4, 5
 GAMMA = 1.4
 
 
@@ -87,6 +89,20 @@ def shock_tube(kind: str = "sod", K: int = 800, N: int = 3, index: int = 0) -> W
         p, t = [rl, ul, pl, rr, ur, pr, 0.5], 0.1
     return Workload("%s_tube_p%d_k%d" % (kind, N, K), 1, PDE_EULER, N, [K], [1], [(0.0, 1.0, 0.0, 1.0)],
                     BC_OUTFLOW, IC_RIEMANN1D, [list(map(float, p))], t)
+
+
+def shock_entropy(K: int = 200, N: int = 2) -> Workload:
+    """Example 9: a Mach-3 shock running into a density wave on [0,1], outflow, to t = 0.178."""
+    p = [3.857143, 2.629369, 10.333333, 0.125, 1.0, 0.2, 16.0 * math.pi, 0.0, 1.0]
+    return Workload("shock_entropy_p%d_k%d" % (N, K), 1, PDE_EULER, N, [K], [1], [(0.0, 1.0, 0.0, 1.0)],
+                    BC_OUTFLOW, IC_SHOCK_ENTROPY, [p], 0.178)
+
+
+def isentropic_vortex(n: int = 40, N: int = 2) -> Workload:
+    """Example 4: the isentropic vortex (x0 = 5, y0 = 0, beta = 5) on [0,10] x [-5,5],
+    periodic, to t = 2 (the domain is our reading; the paper names only the centre)."""
+    return Workload("vortex_p%d_%dx%d" % (N, n, n), 2, PDE_EULER, N, [n], [n], [(0.0, 10.0, -5.0, 5.0)],
+                    BC_PERIODIC, IC_VORTEX, [[5.0, 0.0, 5.0, 0.0]], 2.0)
 
 
 def quadrant_states(rng) -> list:

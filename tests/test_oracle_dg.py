@@ -358,3 +358,38 @@ def test_sod_converges_to_exact_riemann_solution():
         l1, _ = l1_linf_1d(m, u, lambda x: riemann_exact((1, 0, 1), (0.125, 0, 0.1), 1.4, (x - 0.5) / T)[0])
         errs.append(l1)
     assert errs[1] < 0.7 * errs[0] and errs[1] < 6e-3
+
+
+def _table4():
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table4_vortex.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                N, K, a, b = line.split()
+                rows[(int(N), int(K))] = (float(a), float(b))
+    return rows
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_isentropic_vortex_against_table4(N):
+    """Example 4 (domain [0,10] x [-5,5], our reading): the unlimited scheme's density L1
+    errors at t = 2 on 20^2 and 40^2 meshes are within 2.5x of Table 4 (whose mesh is
+    non-uniform) and converge at about N+1; the projected initial state matches the
+    printed exact solution."""
+    from oracle.exact import l1_linf_2d, vortex_exact
+    tab = _table4()
+    errs = []
+    for n in (20, 40):
+        w = W.isentropic_vortex(n, N)
+        m = oracle.Mesh(2, 1, N, n, n, box=w.box[0], bc=w.bc)
+        u = m.project_ic(w.ic, w.params[0])
+        l10, _ = l1_linf_2d(m, u, lambda X, Y: vortex_exact(X, Y, 0.0)[0])
+        assert l10 < tab[(N, n)][0]
+        ws = m.max_wavespeed(u)
+        ns = int(math.ceil(2.0 / (0.1 / (ws[0] * n / 10 + ws[1] * n / 10))))
+        for _ in range(ns):
+            u, _, _ = m.step(u, 2.0 / ns, limit=False)
+        l1, _ = l1_linf_2d(m, u, lambda X, Y: vortex_exact(X, Y, 2.0)[0])
+        assert tab[(N, n)][0] / 2.5 < l1 < tab[(N, n)][0] * 2.5, (N, n, l1)
+        errs.append(l1)
+    assert N + 0.6 < math.log2(errs[0] / errs[1]) < N + 1.8
