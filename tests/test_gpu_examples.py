@@ -71,9 +71,9 @@ def test_vortex_projection_and_unlimited_parity(N):
 def test_vortex_order_and_table4(N):
     """Unlimited runs at 20^2..80^2: P1/P2 L1 errors within 2.5x of Table 4's unlimited
     column (a non-uniform mesh there) and KXRCF-limited runs no worse than 2.5x its limited
-    column; orders about N+1 for all.  P3 converges at the design order but sits 7-15x
-    above Table 4 (the (N+1)-point quadrature of the nonlinear flux on a vortex resolved by
-    two cells per core radius; the paper does not state its quadrature): reported."""
+    column; orders about N+1 for all.  P3 converges at the design order but sits 6-15x
+    above Table 4 (neither a finer time step nor an (N+2)-point volume rule changes its
+    error): reported."""
     tab = _table4()
     for limiter, col in ((None, 0), (dgl.IND_KXRCF, 1)):
         errs = []
