@@ -89,6 +89,8 @@ def lib():
             l.or_step_gen.argtypes = [M, ctypes.c_double, _D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, ctypes.c_double, _L, _L, _L]
             l.or_step_gen.restype = ctypes.c_long
+            l.or_max_wavespeed_points.argtypes = [M, _D, _D]
+            l.or_max_wavespeed_points.restype = ctypes.c_int
             l.or_dg_export.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
             _lib = l
     return _lib
@@ -243,6 +245,14 @@ class Mesh:
         u = self._chk(u)
         out = np.zeros(2)
         lib().or_max_wavespeed(self._ref(), _dp(u), _dp(out))
+        return out
+
+    def max_wavespeed_points(self, u):
+        """Largest |v_d| + c over the positivity check points (Euler), per direction."""
+        u = self._chk(u)
+        out = np.zeros(2)
+        if lib().or_max_wavespeed_points(self._ref(), _dp(u), _dp(out)) != 0:
+            raise ValueError("defined for the Euler equations")
         return out
 
     def project_ic(self, kind, params):

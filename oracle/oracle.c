@@ -1314,6 +1314,55 @@ long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) 
  * and, when pp is set (Euler), the positivity-preserving scaling after the limiter of
  * every stage.  *n_pp (if given) receives the number of cell changes over the three
  * stages and *n_bad the cells whose mean was not admissible. */
+/* Largest characteristic speed |v_d| + c over the check points of the positivity-
+ * preserving scaling (the Gauss-Lobatto points in 1D; Gauss x Gauss-Lobatto and
+ * Gauss-Lobatto x Gauss in 2D), per direction.  Zhang and Shu's condition for admissible
+ * means bounds the time step by the wave speeds of these point values, not of the cell
+ * means.  Points without a real sound speed are skipped.  Euler only (returns -1). */
+int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
+  if (m->pde != 1) return -1;
+  const int dim = m->dim, N = m->N, nv = or_nvars(dim, 1), np = or_nmodes(dim, N);
+  const int L = N == 1 ? 2 : 3;
+  const ld glx[3] = {-1.0L, 0.0L, 1.0L}, glx2[2] = {-1.0L, 1.0L};
+  const ld* gl = L == 2 ? glx2 : glx;
+  ld gx[OR_MAXQ], gw[OR_MAXQ];
+  gauss_rule(N + 1, gx, gw);
+  int npt = 0;
+  double phi[2 * OR_MAXQ * 3][OR_MAXNP];
+  if (dim == 1) {
+    for (int i = 0; i < L; ++i, ++npt)
+      for (int k = 0; k < np; ++k) phi[npt][k] = (double)psi(k, gl[i]);
+  } else {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i <= N; ++i)
+        for (int j = 0; j < L; ++j, ++npt) {
+          const ld r = pass == 0 ? gx[i] : gl[j], t = pass == 0 ? gl[j] : gx[i];
+          for (int k = 0; k < np; ++k) {
+            int a, b;
+            mode_ab(k, &a, &b);
+            phi[npt][k] = (double)(psi(a, r) * psi(b, t));
+          }
+        }
+  }
+  out[0] = out[1] = 0.0;
+  for (size_t c = 0; c < (size_t)m->nx * m->ny; ++c) {
+    const double* uc = u + c * nv * np;
+    for (int q = 0; q < npt; ++q) {
+      double w[OR_MAXV];
+      for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int k = 0; k < np; ++k) s += uc[v * np + k] * phi[q][k];
+        w[v] = s;
+      }
+      for (int d = 0; d < dim; ++d) {
+        const double sp = max_speed(dim, 1, m->gamma, d, w);
+        if (sp > out[d]) out[d] = sp; /* a NaN speed never compares greater */
+      }
+    }
+  }
+  return 0;
+}
+
 long or_step_gen(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,
                  double pp_eps, long* n_near, long* n_pp, long* n_bad);
 long or_step_ind(const or_mesh* m, double dt, double* u, int ind, double M, int limit, double eps, int pp,

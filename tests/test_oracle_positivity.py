@@ -191,3 +191,22 @@ def test_step_with_scaling_keeps_check_points_admissible():
         assert bad == 0
         q = _values(u, Phi)
         assert q[..., 0].min() > 0 and _pressure(q).min() > 0
+
+
+@pytest.mark.parametrize("dim,N", [(1, 1), (1, 3), (2, 2), (2, 3)])
+def test_max_wavespeed_points(dim, N):
+    """The largest |v_d| + c over the check points: equal to the mean-based speed for
+    piecewise-constant data, and to an independent numpy evaluation at the check points in
+    general (points without a real sound speed skipped)."""
+    m = _mesh(dim, N, 7)
+    rng = np.random.default_rng(90 + 10 * dim + N)
+    u = W.random_modes(dim, 1, N, m.nx * m.ny, rng, smooth=0.0)
+    np.testing.assert_array_equal(m.max_wavespeed_points(u), m.max_wavespeed(u))
+    u = _hostile(dim, N, m.nx * m.ny, rng)
+    q = _values(u, _basis(dim, N, _points(dim, N)))
+    rho, p = q[..., 0], _pressure(q)
+    ok = (rho > 0) & (p > 0)
+    c = np.sqrt(np.where(ok, G * p / np.where(ok, rho, 1.0), 0.0))
+    want = [np.max(np.where(ok, np.abs(q[..., 1 + d] / np.where(ok, rho, 1.0)) + c, 0.0)) for d in range(dim)]
+    got = m.max_wavespeed_points(u)[:dim]
+    np.testing.assert_allclose(got, want, rtol=1e-13)
