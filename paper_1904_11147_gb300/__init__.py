@@ -87,6 +87,7 @@ def lib():
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             l.dg_positivity_limit.argtypes = [P, ctypes.c_double]
             l.dg_parent_wenolimit.argtypes = [P]
+            l.dg_max_wavespeed_points.argtypes = [P, D]
             l.dg_set_limiter.argtypes = [P, ctypes.c_int]
             l.dg_set_positivity.argtypes = [P, ctypes.c_int, ctypes.c_double]
             l.dg_positivity_counts.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -97,7 +98,7 @@ def lib():
                          "dg_mlp_get_params", "dg_mlp_set_params", "dg_mlp_grad", "dg_mlp_train_step",
                          "dg_set_indicator_mlp", "dg_indicator_logits", "dg_harvest", "dg_mlp_predict",
                          "dg_positivity_limit", "dg_set_positivity", "dg_positivity_counts",
-                         "dg_parent_wenolimit", "dg_set_limiter"):
+                         "dg_parent_wenolimit", "dg_set_limiter", "dg_max_wavespeed_points"):
                 getattr(l, name).restype = ctypes.c_int
             _lib = l
     return _lib
@@ -239,9 +240,12 @@ class Mesh:
         lib().dg_positivity_counts(self._h, ctypes.byref(a), ctypes.byref(b), int(reset))
         return int(a.value), int(b.value)
 
-    def max_wavespeed(self):
+    def max_wavespeed(self, points=False):
+        """[n_inst][2] largest wave speeds per direction, over the cell means or (points,
+        Euler) over the positivity check points."""
         out = np.zeros(2 * self.n_inst)
-        _check(lib().dg_max_wavespeed(self._h, _dp(out)))
+        fn = lib().dg_max_wavespeed_points if points else lib().dg_max_wavespeed
+        _check(fn(self._h, _dp(out)))
         return out.reshape(self.n_inst, 2)
 
     @property

@@ -77,6 +77,8 @@ void launch_parent(int dim, int pde, int N, const LaunchArgs& a, const int* lc, 
 void launch_kxrcf(int dim, int pde, int N, const LaunchArgs& a, const double* hpow, const double* psi_m1,
                   const double* psi_p1, const double* psi_q, const double* gw, unsigned char* flags, Counters* cnt,
                   int* lc, int* li);
+void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
+                         const int* cell_inst, const double* phi, int npt, double gam, double* out, int nblocks);
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* phi, int npt, double c0, double gam, double eps0,
                        unsigned long long* counts, int nblocks);
@@ -784,6 +786,21 @@ extern "C" dg_status dg_positivity_counts(dg_mesh* m, int64_t* changed, int64_t*
   if (changed) *changed = (int64_t)c[0];
   if (bad_means) *bad_means = (int64_t)c[1];
   return c[1] ? DG_EPOSITIVITY : DG_OK;
+}
+
+extern "C" dg_status dg_max_wavespeed_points(dg_mesh* m, double* out) {
+  if (!m || !out) return fail(DG_EINVAL, "null argument");
+  if (m->pde != DG_EULER) return fail(DG_EINVAL, "the check-point wave speed is defined for the Euler equations");
+  CK(cudaMemsetAsync(m->d_speed, 0, sizeof(double) * 2 * m->n_inst, m->st));
+  const long long want = (m->ncell + 127) / 128;
+  const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
+  launch_speed_points(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->d_cell_inst, m->pp_phi.data(),
+                      m->pp_npt, m->gamma, m->d_speed, nb);
+  m->launches++;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, m->d_speed, sizeof(double) * 2 * m->n_inst, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return DG_OK;
 }
 
 extern "C" dg_status dg_max_wavespeed(dg_mesh* m, double* out) {

@@ -143,6 +143,83 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
   }
 }
 
+// Largest |v_d| + c over the check points of every cell, per instance and direction:
+// out[2 * inst + d] (non-negative doubles, zeroed by the caller).  Points without a real
+// sound speed are skipped (a NaN never wins the comparison).
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__ U, long long ctot, long long ncell,
+                                                      const int* __restrict__ cell_inst, PpTab tb, double gam,
+                                                      double* __restrict__ out) {
+  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
+  constexpr int L = N == 1 ? 2 : 3;
+  constexpr int NPT = DIM == 1 ? L : 2 * (N + 1) * L;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
+    const long long c = base + threadIdx.x;
+    double sm[2] = {0.0, 0.0};
+    int inst = -1;
+    if (c < ncell) {
+      inst = cell_inst[c];
+      double u[V][NP];
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) u[v][k] = U[(long long)(v * NP + k) * ctot + c];
+#pragma unroll 1
+      for (int q = 0; q < NPT; ++q) {
+        double w[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) s = fma(u[v][k], tb.phi[q][k], s);
+          w[v] = s;
+        }
+        const double rho = w[0], vx = w[1] / rho, vy = DIM == 2 ? w[2] / rho : 0.0;
+        const double p = tb.gm1 * (w[V - 1] - 0.5 * rho * (vx * vx + vy * vy));
+        const double cs = sqrt(gam * p / rho);
+        const double sx = fabs(vx) + cs, sy = fabs(vy) + cs;
+        if (sx > sm[0]) sm[0] = sx;
+        if (DIM == 2 && sy > sm[1]) sm[1] = sy;
+      }
+    }
+    // one atomic per warp when the whole warp lies in one instance
+    const int i0 = __shfl_sync(0xffffffffu, inst, 0);
+    const bool same = __all_sync(0xffffffffu, inst == i0 || inst < 0);
+    if (same) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        double m = sm[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && i0 >= 0) atomic_max_nonneg(out + 2 * i0 + d, m);
+      }
+    } else if (inst >= 0) {
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) atomic_max_nonneg(out + 2 * inst + d, sm[d]);
+    }
+  }
+}
+
+void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
+                         const int* cell_inst, const double* phi, int npt, double gam, double* out, int nblocks) {
+  PpTab tb{};
+  const int NP = np_of(dim, N);
+  for (int q = 0; q < npt && q < kPpMaxPts; ++q)
+    for (int k = 0; k < NP; ++k) tb.phi[q][k] = phi[q * NP + k];
+  tb.gm1 = gam - 1.0;
+#define DG_SP(D, NN) k_speed_points<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, ncell, cell_inst, tb, gam, out)
+  if (dim == 1) {
+    if (N == 1) DG_SP(1, 1);
+    else if (N == 2) DG_SP(1, 2);
+    else DG_SP(1, 3);
+  } else {
+    if (N == 1) DG_SP(2, 1);
+    else if (N == 2) DG_SP(2, 2);
+    else DG_SP(2, 3);
+  }
+#undef DG_SP
+}
+
 // phi: [npt][NP] basis values at the check points (host-built from the library tables)
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* phi, int npt, double c0, double gam, double eps0,
