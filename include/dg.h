@@ -185,11 +185,12 @@ dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M);
  * Synchronises the stream. */
 dg_status dg_max_wavespeed(dg_mesh* m, double* out);
 
-/* As dg_max_wavespeed, over the check points of the positivity-preserving scaling instead
- * of the cell means (Euler): the wave speeds that bound the time step under which the
- * scaling keeps the next stage's means admissible (Zhang and Shu).  Points without a real
- * sound speed are skipped.  out: host [n_inst][2].  Synchronises the stream.
- * Errors: DG_EINVAL (Burgers). */
+/* A wave-speed bound over the check points of the positivity-preserving scaling instead of
+ * the cell means (Euler): per instance and direction, max |v_d| + max c over the points of
+ * all cells, which bounds the wave speeds of the face states and so the time step under
+ * which the scaling keeps the next stage's means admissible (Zhang and Shu).  Points
+ * without a real sound speed are skipped.  out: host [n_inst][2].  Synchronises the
+ * stream.  Errors: DG_EINVAL (Burgers). */
 dg_status dg_max_wavespeed_points(dg_mesh* m, double* out);
 
 /* Autotuner: times the candidate launch configurations on this mesh's current state with

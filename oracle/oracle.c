@@ -1314,11 +1314,12 @@ long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) 
  * and, when pp is set (Euler), the positivity-preserving scaling after the limiter of
  * every stage.  *n_pp (if given) receives the number of cell changes over the three
  * stages and *n_bad the cells whose mean was not admissible. */
-/* Largest characteristic speed |v_d| + c over the check points of the positivity-
- * preserving scaling (the Gauss-Lobatto points in 1D; Gauss x Gauss-Lobatto and
- * Gauss-Lobatto x Gauss in 2D), per direction.  Zhang and Shu's condition for admissible
- * means bounds the time step by the wave speeds of these point values, not of the cell
- * means.  Points without a real sound speed are skipped.  Euler only (returns -1). */
+/* Wave-speed bound over the check points of the positivity-preserving scaling (the
+ * Gauss-Lobatto points in 1D; Gauss x Gauss-Lobatto and Gauss-Lobatto x Gauss in 2D), per
+ * direction: max |v_d| + max c over the points of every cell (an upper bound of the
+ * largest |v_d| + c with one square root per cell).  Zhang and Shu's condition for
+ * admissible means bounds the time step by the wave speeds of these point values, not of
+ * the cell means.  Points without a real sound speed are skipped.  Euler only (-1). */
 int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
   if (m->pde != 1) return -1;
   const int dim = m->dim, N = m->N, nv = or_nvars(dim, 1), np = or_nmodes(dim, N);
@@ -1347,6 +1348,7 @@ int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
   out[0] = out[1] = 0.0;
   for (size_t c = 0; c < (size_t)m->nx * m->ny; ++c) {
     const double* uc = u + c * nv * np;
+    double vmax[2] = {0.0, 0.0}, c2max = 0.0;
     for (int q = 0; q < npt; ++q) {
       double w[OR_MAXV];
       for (int v = 0; v < nv; ++v) {
@@ -1354,11 +1356,17 @@ int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
         for (int k = 0; k < np; ++k) s += uc[v * np + k] * phi[q][k];
         w[v] = s;
       }
-      for (int d = 0; d < dim; ++d) {
-        const double sp = max_speed(dim, 1, m->gamma, d, w);
-        if (sp > out[d]) out[d] = sp; /* a NaN speed never compares greater */
-      }
+      const double vx = w[1] / w[0], vy = dim == 2 ? w[2] / w[0] : 0.0;
+      const double p = (m->gamma - 1.0) * (w[nv - 1] - 0.5 * w[0] * (vx * vx + vy * vy));
+      const double c2 = m->gamma * p / w[0];
+      if (!(c2 >= 0.0)) continue; /* no real sound speed (or NaN) */
+      if (c2 > c2max) c2max = c2;
+      if (fabs(vx) > vmax[0]) vmax[0] = fabs(vx);
+      if (fabs(vy) > vmax[1]) vmax[1] = fabs(vy);
     }
+    const double cs = sqrt(c2max);
+    for (int d = 0; d < dim; ++d)
+      if (vmax[d] + cs > out[d]) out[d] = vmax[d] + cs;
   }
   return 0;
 }

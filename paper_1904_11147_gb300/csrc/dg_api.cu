@@ -78,9 +78,10 @@ void launch_kxrcf(int dim, int pde, int N, const LaunchArgs& a, const double* hp
                   const double* psi_p1, const double* psi_q, const double* gw, unsigned char* flags, Counters* cnt,
                   int* lc, int* li);
 void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
-                         const int* cell_inst, const double* phi, int npt, double gam, double* out, int nblocks);
+                         const int* cell_inst, const double* pg, const double* pl, double gam, double* out,
+                         int nblocks);
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
-                       const double* phi, int npt, double c0, double gam, double eps0,
+                       const double* pg, const double* pl, double c0, double gam, double eps0,
                        unsigned long long* counts, int nblocks);
 }  // namespace dg
 
@@ -184,8 +185,7 @@ struct dg_mesh {
   double psi_q[16], psi_p1[4];
   // positivity-preserving scaling (Euler): basis values at the check points, the
   // dg_step option and the running counts (cells changed, inadmissible means)
-  std::vector<double> pp_phi;
-  int pp_npt = 0;
+  double pp_g[16], pp_l[12];  // psi_n at the Gauss [N+1][N+1] and Gauss-Lobatto [L][N+1] points
   bool pp_on = false;
   double pp_eps0 = 1e-13;
   unsigned long long* pp_counts = nullptr;
@@ -395,27 +395,16 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
     dg_mesh_destroy(m);
     return fail(DG_ECUDA, "mesh upload: %s", cudaGetErrorString(e));
   }
-  if (pde == DG_EULER) {
-    // check points of the positivity-preserving scaling: Gauss-Lobatto points (-1, 0, 1;
-    // -1, 1 for N = 1) in 1D; (Gauss x Gauss-Lobatto) then (Gauss-Lobatto x Gauss) in 2D
+  {
+    // 1D bases at the check points of the positivity-preserving scaling: the N+1 Gauss
+    // points and the Gauss-Lobatto points -1, 0, 1 (-1, 1 for N = 1)
     const dgt::Tabs& tb = g_tabs[N - 1];
-    const int L = N == 1 ? 2 : 3;
     const double* gl[3] = {tb.psi_m1, N == 1 ? tb.psi_p1 : tb.psi_0, tb.psi_p1};
-    const int NP = m->NP;
-    if (dim == 1) {
-      for (int j = 0; j < L; ++j)
-        for (int k = 0; k < NP; ++k) m->pp_phi.push_back(gl[j][k]);
-      m->pp_npt = L;
-    } else {
-      for (int pass = 0; pass < 2; ++pass)
-        for (int i = 0; i <= N; ++i)
-          for (int j = 0; j < L; ++j)
-            for (int k = 0; k < NP; ++k) {
-              const int a = mode_a(k), b = mode_b(k);
-              m->pp_phi.push_back(pass == 0 ? tb.psi_q[i][a] * gl[j][b] : gl[j][a] * tb.psi_q[i][b]);
-            }
-      m->pp_npt = 2 * (N + 1) * L;
-    }
+    const int L = N == 1 ? 2 : 3;
+    for (int i = 0; i <= N; ++i)
+      for (int k = 0; k <= N; ++k) m->pp_g[i * (N + 1) + k] = tb.psi_q[i][k];
+    for (int j = 0; j < L; ++j)
+      for (int k = 0; k <= N; ++k) m->pp_l[j * (N + 1) + k] = gl[j][k];
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
@@ -570,8 +559,8 @@ static void k_limit(dg_mesh* m) {
 static void k_pp(dg_mesh* m, double eps0) {
   const long long want = (m->ncell + 127) / 128;
   const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
-  launch_positivity(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->pp_phi.data(), m->pp_npt,
-                    mean_factor(m), m->gamma, eps0, m->pp_counts, nb);
+  launch_positivity(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->pp_g, m->pp_l, mean_factor(m),
+                    m->gamma, eps0, m->pp_counts, nb);
   m->launches++;
 }
 
@@ -794,8 +783,8 @@ extern "C" dg_status dg_max_wavespeed_points(dg_mesh* m, double* out) {
   CK(cudaMemsetAsync(m->d_speed, 0, sizeof(double) * 2 * m->n_inst, m->st));
   const long long want = (m->ncell + 127) / 128;
   const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
-  launch_speed_points(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->d_cell_inst, m->pp_phi.data(),
-                      m->pp_npt, m->gamma, m->d_speed, nb);
+  launch_speed_points(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->d_cell_inst, m->pp_g, m->pp_l,
+                      m->gamma, m->d_speed, nb);
   m->launches++;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, m->d_speed, sizeof(double) * 2 * m->n_inst, cudaMemcpyDeviceToHost, m->st));

@@ -309,7 +309,9 @@ cudaError_t upload_tables_parent(const dgt::Tabs* tabs /* [3], built with parent
 
 void launch_parent(int dim, int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
                    double* lim, int nblocks) {
-#define DG_PW(K, P, NN) pw::K<P, NN><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam)
+  // one warp per block, four times the usual grid: the troubled-cell count is known only on
+  // the device, and small lists then still spread over all SMs
+#define DG_PW(K, P, NN) pw::K<P, NN><<<4 * nblocks, 32, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam)
 #define DG_PW_N(K, P)  \
   do {                 \
     if (N == 1) DG_PW(K, P, 1); \

@@ -18,12 +18,67 @@
 
 namespace dg {
 
-constexpr int kPpMaxPts = 24;  // 2D P3: 2 x 4 x 3
-
 struct PpTab {
-  double phi[kPpMaxPts][10];  // basis values [point][mode]
+  double pg[4][4];  // psi_n at the N+1 Gauss points [i][n]
+  double pl[3][4];  // psi_n at the L Gauss-Lobatto points [j][n] (-1, 0, 1; or -1, 1 for N = 1)
   double c0, gm1, eps0;
 };
+
+// Calls f(w) with the V point values of the modes u[0..V-1] at every check point: in 1D
+// the Gauss-Lobatto points; in 2D (Gauss x Gauss-Lobatto) then (Gauss-Lobatto x Gauss),
+// by sum factorisation over the Gauss coordinate.
+template <int DIM, int N, int V, class F>
+__device__ __forceinline__ void for_points(const double (*u)[np_of(DIM, N)], const PpTab& tb, F&& f) {
+  constexpr int L = N == 1 ? 2 : 3, NP = np_of(DIM, N);
+  if constexpr (DIM == 1) {
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      double w[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) s = fma(u[v][k], tb.pl[j][k], s);
+        w[v] = s;
+      }
+      f(w);
+    }
+  } else {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+      for (int i = 0; i <= N; ++i) {
+        // pass 0: t_b = sum_a U_ab psi_a(g_i), point (g_i, l_j) = sum_b t_b psi_b(l_j)
+        // pass 1: t_a = sum_b U_ab psi_b(g_i), point (l_j, g_i) = sum_a t_a psi_a(l_j)
+        double t[V][N + 1];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int c = 0; c <= N; ++c) {
+            double s = 0.0;
+#pragma unroll
+            for (int d = 0; d <= N - c; ++d) {
+              const int m = pass == 0 ? mode_idx(d, c) : mode_idx(c, d);
+              s = fma(u[v][m], tb.pg[i][d], s);
+            }
+            t[v][c] = s;
+          }
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+          double w[V];
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c <= N; ++c) s = fma(t[v][c], tb.pl[j][c], s);
+            w[v] = s;
+          }
+          f(w);
+        }
+      }
+    }
+  }
+}
 
 template <int V>
 __device__ __forceinline__ double pp_pressure(const double* q, double gm1) {
@@ -60,13 +115,14 @@ __device__ __forceinline__ double pp_root(const double* ub, const double* uq, do
   return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
 }
 
-// counts[0] += cells changed, counts[1] += cells whose mean is not admissible
+// counts[0] += cells changed, counts[1] += cells whose mean is not admissible.  The
+// density pass gives rho_min; the pressure pass evaluates every variable of the unscaled
+// state and applies the density factor to the density point values (rho' = rhobar +
+// theta1 (rho - rhobar), the point values of the scaled modes).
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long long ctot, long long ncell,
                                                     PpTab tb, unsigned long long* __restrict__ counts) {
   constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
-  constexpr int L = N == 1 ? 2 : 3;
-  constexpr int NPT = DIM == 1 ? L : 2 * (N + 1) * L;
   unsigned int n_changed = 0, n_bad = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -86,50 +142,35 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
     double eps = tb.eps0;
     if (ub[0] < eps) eps = ub[0];
     if (pb < eps) eps = pb;
-    bool touched = false;
     double rmin = ub[0];
-#pragma unroll 1
-    for (int q = 0; q < NPT; ++q) {
-      double r = 0.0;
-#pragma unroll
-      for (int k = 0; k < NP; ++k) r = fma(u[0][k], tb.phi[q][k], r);
-      if (r < rmin) rmin = r;
-    }
-    if (rmin < eps) {
-      const double th1 = (ub[0] - eps) / (ub[0] - rmin);
-#pragma unroll
-      for (int k = 1; k < NP; ++k) u[0][k] *= th1;
-      touched = true;
-    }
+    for_points<DIM, N, 1>(u, tb, [&](const double* w) {
+      if (w[0] < rmin) rmin = w[0];
+    });
+    double th1 = 1.0;
+    if (rmin < eps) th1 = (ub[0] - eps) / (ub[0] - rmin);
     double th2 = 1.0;
-#pragma unroll 1
-    for (int q = 0; q < NPT; ++q) {
-      double uq[V];
+    for_points<DIM, N, V>(u, tb, [&](const double* w) {
+      double q[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) s = fma(u[v][k], tb.phi[q][k], s);
-        uq[v] = s;
-      }
-      if (pp_pressure<V>(uq, tb.gm1) < eps) {
-        const double t = pp_root<V>(ub, uq, eps, tb.gm1);
+      for (int v = 0; v < V; ++v) q[v] = w[v];
+      if (th1 < 1.0) q[0] = fma(th1, w[0] - ub[0], ub[0]);
+      // p < eps tested as rho p < eps rho (rho >= eps > 0 here): no division per point
+      double k2 = q[1] * q[1];
+      if (V == 4) k2 = fma(q[2], q[2], k2);
+      const double rp = tb.gm1 * fma(q[V - 1], q[0], -0.5 * k2);
+      if (rp < eps * q[0]) {
+        const double t = pp_root<V>(ub, q, eps, tb.gm1);
         if (t < th2) th2 = t;
       }
-    }
-    if (th2 < 1.0) {
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-#pragma unroll
-        for (int k = 1; k < NP; ++k) u[v][k] *= th2;
-      touched = true;
-    }
-    if (touched) {
+    });
+    if (th1 < 1.0 || th2 < 1.0) {
       ++n_changed;
 #pragma unroll
-      for (int v = 0; v < V; ++v)
+      for (int v = 0; v < V; ++v) {
+        const double f = v == 0 ? th1 * th2 : th2;
 #pragma unroll
-        for (int k = 1; k < NP; ++k) U[(long long)(v * NP + k) * ctot + c] = u[v][k];
+        for (int k = 1; k < NP; ++k) U[(long long)(v * NP + k) * ctot + c] = u[v][k] * f;
+      }
     }
   }
 #pragma unroll
@@ -143,16 +184,15 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
   }
 }
 
-// Largest |v_d| + c over the check points of every cell, per instance and direction:
-// out[2 * inst + d] (non-negative doubles, zeroed by the caller).  Points without a real
-// sound speed are skipped (a NaN never wins the comparison).
+// Wave-speed bound over the check points of every cell, per instance and direction:
+// out[2 * inst + d] = max |v_d| + max c over the points (one square root per cell), the
+// non-negative doubles zeroed by the caller.  Points without a real sound speed are
+// skipped (a NaN never wins the comparison).
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__ U, long long ctot, long long ncell,
                                                       const int* __restrict__ cell_inst, PpTab tb, double gam,
                                                       double* __restrict__ out) {
   constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
-  constexpr int L = N == 1 ? 2 : 3;
-  constexpr int NPT = DIM == 1 ? L : 2 * (N + 1) * L;
   for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
     const long long c = base + threadIdx.x;
     double sm[2] = {0.0, 0.0};
@@ -164,23 +204,20 @@ __global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__
       for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int k = 0; k < NP; ++k) u[v][k] = U[(long long)(v * NP + k) * ctot + c];
-#pragma unroll 1
-      for (int q = 0; q < NPT; ++q) {
-        double w[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          double s = 0.0;
-#pragma unroll
-          for (int k = 0; k < NP; ++k) s = fma(u[v][k], tb.phi[q][k], s);
-          w[v] = s;
+      double vmax[2] = {0.0, 0.0}, c2max = 0.0;
+      for_points<DIM, N, V>(u, tb, [&](const double* w) {
+        const double r = 1.0 / w[0], vx = w[1] * r, vy = DIM == 2 ? w[2] * r : 0.0;
+        const double p = tb.gm1 * (w[V - 1] - 0.5 * w[0] * (vx * vx + vy * vy));
+        const double c2 = gam * p * r;
+        if (c2 >= 0.0) {  // a real sound speed (false for NaN)
+          if (c2 > c2max) c2max = c2;
+          if (fabs(vx) > vmax[0]) vmax[0] = fabs(vx);
+          if (DIM == 2 && fabs(vy) > vmax[1]) vmax[1] = fabs(vy);
         }
-        const double rho = w[0], vx = w[1] / rho, vy = DIM == 2 ? w[2] / rho : 0.0;
-        const double p = tb.gm1 * (w[V - 1] - 0.5 * rho * (vx * vx + vy * vy));
-        const double cs = sqrt(gam * p / rho);
-        const double sx = fabs(vx) + cs, sy = fabs(vy) + cs;
-        if (sx > sm[0]) sm[0] = sx;
-        if (DIM == 2 && sy > sm[1]) sm[1] = sy;
-      }
+      });
+      const double cs = sqrt(c2max);
+      sm[0] = vmax[0] + cs;
+      if (DIM == 2) sm[1] = vmax[1] + cs;
     }
     // one atomic per warp when the whole warp lies in one instance
     const int i0 = __shfl_sync(0xffffffffu, inst, 0);
@@ -200,13 +237,24 @@ __global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__
   }
 }
 
-void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
-                         const int* cell_inst, const double* phi, int npt, double gam, double* out, int nblocks) {
+static PpTab make_tab(int N, const double* pg, const double* pl, double c0, double gam, double eps0) {
   PpTab tb{};
-  const int NP = np_of(dim, N);
-  for (int q = 0; q < npt && q < kPpMaxPts; ++q)
-    for (int k = 0; k < NP; ++k) tb.phi[q][k] = phi[q * NP + k];
+  const int L = N == 1 ? 2 : 3;
+  for (int i = 0; i <= N; ++i)
+    for (int k = 0; k <= N; ++k) tb.pg[i][k] = pg[i * (N + 1) + k];
+  for (int j = 0; j < L; ++j)
+    for (int k = 0; k <= N; ++k) tb.pl[j][k] = pl[j * (N + 1) + k];
+  tb.c0 = c0;
   tb.gm1 = gam - 1.0;
+  tb.eps0 = eps0;
+  return tb;
+}
+
+// pg: psi_n at the Gauss points [(N+1)][(N+1)], pl: at the Gauss-Lobatto points [L][(N+1)]
+void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
+                         const int* cell_inst, const double* pg, const double* pl, double gam, double* out,
+                         int nblocks) {
+  const PpTab tb = make_tab(N, pg, pl, 0.0, gam, 0.0);
 #define DG_SP(D, NN) k_speed_points<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, ncell, cell_inst, tb, gam, out)
   if (dim == 1) {
     if (N == 1) DG_SP(1, 1);
@@ -220,17 +268,10 @@ void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long 
 #undef DG_SP
 }
 
-// phi: [npt][NP] basis values at the check points (host-built from the library tables)
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
-                       const double* phi, int npt, double c0, double gam, double eps0,
+                       const double* pg, const double* pl, double c0, double gam, double eps0,
                        unsigned long long* counts, int nblocks) {
-  PpTab tb{};
-  const int NP = np_of(dim, N);
-  for (int q = 0; q < npt && q < kPpMaxPts; ++q)
-    for (int k = 0; k < NP; ++k) tb.phi[q][k] = phi[q * NP + k];
-  tb.c0 = c0;
-  tb.gm1 = gam - 1.0;
-  tb.eps0 = eps0;
+  const PpTab tb = make_tab(N, pg, pl, c0, gam, eps0);
 #define DG_PP(D, NN) k_positivity<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, ncell, tb, counts)
   if (dim == 1) {
     if (N == 1) DG_PP(1, 1);
