@@ -416,8 +416,8 @@ def main():
         "config": {"workload": w.name, "cells": n * n, "dofs": dofs, "dt": dt,
                    "indicator": "learned (TVB-gated MLP)" if args.arms == "both" else "tvb",
                    "tvb_M": 0.01, "limiter": "cswenolimit", "graph": True,
-                   "autotuned": {"stage_tile_rows": tune[0], "limiter_blocks_per_sm": tune[1],
-                                 "stage_persistent_queue": bool(tune[2])},
+                   "autotuned": {"stage_form": "split" if tune[0] == 0 else "fused", "stage_tile_rows": tune[0],
+                                 "limiter_blocks_per_sm": tune[1], "stage_persistent_queue": bool(tune[2])},
                    "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "learned": {"value": value, "ms_per_step": ms / args.steps, "limited_fraction": lim_learned, "tau": tau,
@@ -553,8 +553,8 @@ def batched_arm(args, dist, rank, world, torch, dgl):
                        "time_step": "per step from check-point wave speeds (CFL 0.1), timed" if euler
                        else "fixed at the initial state (CFL 0.1)",
                        "limiter": "cswenolimit", "graph": True, "per_instance_dt": True,
-                       "autotuned": {"stage_tile_rows": tune[0], "limiter_blocks_per_sm": tune[1],
-                                     "stage_persistent_queue": bool(tune[2])},
+                       "autotuned": {"stage_form": "split" if tune[0] == 0 else "fused", "stage_tile_rows": tune[0],
+                                     "limiter_blocks_per_sm": tune[1], "stage_persistent_queue": bool(tune[2])},
                        "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "plain": plain, "gpu_launches": launches, "clocks": clk.summary()}

@@ -195,10 +195,14 @@ dg_status dg_max_wavespeed_points(dg_mesh* m, double* out);
 
 /* Autotuner: times the candidate launch configurations on this mesh's current state with
  * the time step dt (u^n is left unchanged; stage buffers and limiter scratch are
- * overwritten): the 2D stage kernel's tile height (4 or 8 rows of 32 cells plus their
- * halo warps) and launch form (one block per tile, or one persistent block per SM taking
- * tiles from an atomic queue), and the limiter's grid (2, 4, 8 or 16 blocks per SM).
- * Applies the fastest
+ * overwritten): the 2D stage form -- split into a face pass (one thread per face: traces,
+ * local Lax-Friedrichs flux, projection onto the transverse modes) and a cell pass (volume
+ * term, lifting, stage combination), reported as stage_ty = 0, or fused in one kernel per
+ * tile with a tile height of 4 or 8 rows of 32 cells plus their halo warps and launched
+ * one block per tile or as one persistent block per SM taking tiles from an atomic queue --
+ * and the limiter's grid (2, 4, 8 or 16 blocks per SM).  The split form is the default of
+ * a 2D mesh (it needs (N+1) x V doubles per face; without that memory the mesh uses the
+ * fused form).  Applies the fastest
  * to the mesh and remembers them for later meshes of the same dim, PDE, N and size class
  * (floor(log2 cells)); with the environment variable DG_AUTOTUNE_FILE set, choices are also
  * appended to that file and read back by later processes.  Synchronises the stream.

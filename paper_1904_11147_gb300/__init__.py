@@ -263,8 +263,9 @@ class Mesh:
         _check(lib().dg_set_indicator_mlp(self._h, net._h, tau))
 
     def autotune(self, dt):
-        """Chooses the stage tile height and launch form and the limiter grid on this mesh
-        (see dg_autotune); returns (tile rows, limiter blocks per SM, persistent)."""
+        """Chooses the stage form (split, or fused with its tile height and launch form) and
+        the limiter grid on this mesh (see dg_autotune); returns (tile rows, 0 for the split
+        stage; limiter blocks per SM; persistent)."""
         a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         _check(lib().dg_autotune(self._h, dt, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return int(a.value), int(b.value), int(c.value)

@@ -31,6 +31,8 @@ void launch_scatter1(int pde, int N, const LaunchArgs& a, const double* lim, con
 void launch_project1(int pde, int N, const LaunchArgs& a, const int* cell_inst, int kind, const double* params, int np);
 void launch_speed1(int pde, int N, const LaunchArgs& a, const int* cell_inst, double* out);
 void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all, int tys, int* queue, int grid);
+void launch_stage2_split(int pde, int N, const LaunchArgs& a, int stage, double dt_all, const Tile* face_tiles,
+                         int nface_tiles, double* fx, long long fxt, double* fy, long long fyt);
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc, int* li);
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt, double* lim,
                    int nblocks);
@@ -163,6 +165,13 @@ struct dg_mesh {
   int n_stage_tiles = 0;
   int stage_persistent = 0;  // persistent tile queue (1) or one block per tile (0)
   int* d_queue = nullptr;
+  // split 2D stage (face pass + cell pass; stage_ty == 0): face flux planes, x faces then
+  // y faces, with their plane strides, and the face tiles
+  bool stage_split = false;
+  double* fbuf = nullptr;
+  long long fxt = 0, fyt = 0;
+  Tile* d_face_tiles = nullptr;
+  int n_face_tiles = 0;
   long long launches = 0;
   // CUDA graph of one full step
   cudaGraphExec_t gexec = nullptr;
@@ -214,6 +223,8 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_tiles);
   cudaFree(m->d_stage_tiles);
   cudaFree(m->d_queue);
+  cudaFree(m->fbuf);
+  cudaFree(m->d_face_tiles);
   cudaFree(m->d_cell_inst);
   for (auto& p : m->U) cudaFree(p);
   cudaFree(m->lim);
@@ -235,7 +246,8 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
 // ----------------------------------------------------------------------------- autotuning
 // Process-wide choices per (dim, pde, N, mesh-size class = floor(log2 cells)); optionally
 // loaded from and appended to the text file named by DG_AUTOTUNE_FILE
-// ("dim pde N class stage_ty limit_blocks_per_sm persistent" per line).
+// ("dim pde N class stage_ty limit_blocks_per_sm persistent" per line; stage_ty 0 = the
+// split face/cell stage, 4 or 8 = the fused stage's tile height).
 struct TuneKey {
   int dim, pde, N, cls;
   bool operator==(const TuneKey& o) const { return dim == o.dim && pde == o.pde && N == o.N && cls == o.cls; }
@@ -263,7 +275,7 @@ static void tune_load() {
   TuneVal v;
   while (fscanf(fp, "%d %d %d %d %d %d %d", &k.dim, &k.pde, &k.N, &k.cls, &v.stage_ty, &v.limit_per_sm,
                 &v.persistent) == 7)
-    if ((v.stage_ty == 4 || v.stage_ty == 8) && v.limit_per_sm >= 1 && v.limit_per_sm <= 64 &&
+    if ((v.stage_ty == 0 || v.stage_ty == 4 || v.stage_ty == 8) && v.limit_per_sm >= 1 && v.limit_per_sm <= 64 &&
         (v.persistent == 0 || v.persistent == 1))
       g_tune.push_back({k, v});
   fclose(fp);
@@ -312,7 +324,7 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   m->NP = np_of(dim, N);
   m->st = (cudaStream_t)stream;
   cudaGetDevice(&m->device);
-  long long off = 0;
+  long long off = 0, fxoff = 0, fyoff = 0;
   std::vector<Tile> tiles;
   const int TW = dim == 1 ? tile_w1() : tile_w2(), TH = dim == 1 ? 1 : tile_h2();
   for (int i = 0; i < n_inst; ++i) {
@@ -334,6 +346,10 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
     I.xL = xL;
     I.yL = dim == 2 ? yL : 0.0;
     I.dt = 0.0;
+    I.fx = fxoff;
+    I.fy = fyoff;
+    fxoff += (long long)(I.nx + 1) * I.ny;
+    fyoff += (long long)I.nx * (I.ny + 1);
     m->h_inst.push_back(I);
     for (int y0 = 0; y0 < I.ny; y0 += TH)
       for (int x0 = 0; x0 < I.nx; x0 += TW) tiles.push_back(Tile{i, x0, y0, 0});
@@ -417,10 +433,36 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (dim == 2) {
     e = prepare2(pde, N);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_queue, sizeof(int));
-    if (e == cudaSuccess) e = build_stage_tiles(m, tv ? tv->stage_ty : 8);
+    if (e == cudaSuccess) e = build_stage_tiles(m, tv && tv->stage_ty ? tv->stage_ty : 8);
     if (e != cudaSuccess) {
       dg_mesh_destroy(m);
       return fail(DG_ECUDA, "stage kernel set-up: %s", cudaGetErrorString(e));
+    }
+    // split stage: face planes and face tiles (32 faces x 4 rows); without the memory the
+    // mesh keeps the fused stage
+    std::vector<Tile> ft;
+    for (int i = 0; i < n_inst; ++i) {
+      const Inst& I = m->h_inst[i];
+      for (int y0 = 0; y0 < I.ny; y0 += 4)
+        for (int x0 = 0; x0 <= I.nx; x0 += 32) ft.push_back(Tile{i, x0, y0, 0});
+      for (int y0 = 0; y0 <= I.ny; y0 += 4)
+        for (int x0 = 0; x0 < I.nx; x0 += 32) ft.push_back(Tile{i, x0, y0, 1});
+    }
+    m->fxt = (fxoff + 31) / 32 * 32;
+    m->fyt = (fyoff + 31) / 32 * 32;
+    const size_t fbytes = sizeof(double) * (size_t)(m->N + 1) * m->V * (size_t)(m->fxt + m->fyt);
+    if (cudaMalloc(&m->fbuf, fbytes) == cudaSuccess &&
+        cudaMalloc(&m->d_face_tiles, sizeof(Tile) * ft.size()) == cudaSuccess &&
+        cudaMemcpy(m->d_face_tiles, ft.data(), sizeof(Tile) * ft.size(), cudaMemcpyHostToDevice) == cudaSuccess) {
+      m->n_face_tiles = (int)ft.size();
+      m->stage_split = !tv || tv->stage_ty == 0;
+    } else {
+      cudaGetLastError();
+      cudaFree(m->fbuf);
+      cudaFree(m->d_face_tiles);
+      m->fbuf = nullptr;
+      m->d_face_tiles = nullptr;
+      m->stage_split = false;
     }
   }
   *out = m;
@@ -451,6 +493,13 @@ static void k_stage(dg_mesh* m, int stage, int in, int out, double dt_all) {
     launch_stage1(m->pde, m->N, args<LaunchArgs>(m, 0, in, out), stage, dt_all);
   } else {
     LaunchArgs a = args<LaunchArgs>(m, 0, in, out);
+    if (m->stage_split) {
+      double* fy = m->fbuf + (size_t)(m->N + 1) * m->V * m->fxt;
+      launch_stage2_split(m->pde, m->N, a, stage, dt_all, m->d_face_tiles, m->n_face_tiles, m->fbuf, m->fxt, fy,
+                          m->fyt);
+      m->launches += 2;
+      return;
+    }
     a.tiles = m->d_stage_tiles;
     a.ntiles = m->n_stage_tiles;
     if (m->stage_persistent) cudaMemsetAsync(m->d_queue, 0, sizeof(int), m->st);
@@ -888,9 +937,9 @@ extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M)
 }
 
 // Times the candidate configurations on this mesh's current state (u^n is left unchanged):
-// the 2D stage tile height (4 or 8 rows) and launch form (one block per tile, or a
-// persistent grid taking tiles from a queue) on stage 1, then the limiter's grid (2, 4, 8
-// or 16 blocks per SM) on the TVB-flagged cells of that stage.  The fastest are applied to the
+// the 2D stage form on stage 1 -- split (face pass + cell pass) or fused with a tile height
+// of 4 or 8 rows and one block per tile or a persistent grid taking tiles from a queue --
+// then the limiter's grid (2, 4, 8 or 16 blocks per SM) on the TVB-flagged cells of that stage.  The fastest are applied to the
 // mesh and remembered for meshes of the same kind and size class.
 extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limit_blocks_per_sm, int* persistent) {
   if (!m || !(dt > 0.0)) return fail(DG_EINVAL, "bad arguments");
@@ -913,9 +962,15 @@ extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limi
     return best;
   };
   m->cur = 0;
-  int best_ty = m->stage_ty, best_pers = m->stage_persistent;
+  int best_ty = m->stage_split ? 0 : m->stage_ty, best_pers = m->stage_persistent;
   if (m->dim == 2) {
     float best = 1e30f;
+    if (m->fbuf) {  // split stage (face pass + cell pass)
+      m->stage_split = true;
+      best = time_it([&] { k_stage(m, 1, 0, 1, dt); }, 3);
+      best_ty = 0;
+    }
+    m->stage_split = false;
     for (int ty : {8, 4}) {
       cudaError_t e = build_stage_tiles(m, ty);
       if (e != cudaSuccess) return fail(DG_ECUDA, "stage tiles: %s", cudaGetErrorString(e));
@@ -925,8 +980,9 @@ extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limi
         if (ms < best) { best = ms; best_ty = ty; best_pers = pers; }
       }
     }
-    CK(build_stage_tiles(m, best_ty));
+    CK(build_stage_tiles(m, best_ty ? best_ty : 8));
     m->stage_persistent = best_pers;
+    m->stage_split = best_ty == 0;
   }
   // limiter grid on the flagged cells of stage 1 (writes only the limiter scratch)
   k_stage(m, 1, 0, 1, dt);

@@ -33,6 +33,7 @@ struct Inst {
   double hx, hy;  // cell widths
   double xL, yL;  // lower-left corner
   double dt;      // per-instance time step (dg_set_dt)
+  long long fx, fy;  // first x face / y face of the instance in the 2D face planes
 };
 
 // A tile of the 2D stage / flag kernels: instance and lower-left cell of the tile.
@@ -130,6 +131,21 @@ __device__ __forceinline__ void llf(int dir, const double* uL, const double* uR,
   const double a = nan_lr ? aL + aR : fmax(aL, aR);
 #pragma unroll
   for (int v = 0; v < V; ++v) fs[v] = inv_h * fma(-a, uR[v] - uL[v], fL[v] + fR[v]);
+}
+
+// The same flux without the 1/h factor: fs = (fL + fR) - alpha (uR - uL) = 2 f*.
+template <int DIM, int PDE>
+__device__ __forceinline__ void llf_sum(int dir, const double* uL, const double* uR, double* fs, double gam,
+                                        double gm1) {
+  constexpr int V = Phys<DIM, PDE>::V;
+  double fL[V], fR[V], aL, aR;
+  Phys<DIM, PDE>::flux(dir, uL, fL, aL, gam, gm1);
+  Phys<DIM, PDE>::flux(dir, uR, fR, aR, gam, gm1);
+  constexpr unsigned long long kAbs = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+  const bool nan_lr = ((__double_as_longlong(aL) & kAbs) > kInf) | ((__double_as_longlong(aR) & kAbs) > kInf);
+  const double a = nan_lr ? aL + aR : fmax(aL, aR);
+#pragma unroll
+  for (int v = 0; v < V; ++v) fs[v] = fma(-a, uR[v] - uL[v], fL[v] + fR[v]);
 }
 
 }  // namespace dg

@@ -497,6 +497,249 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
 #undef sE
 #undef sN
 
+// ----------------------------------------------------------------------------- split stage
+// The same stage of Eq. (5) as two passes without block barriers or halo work:
+//   k_face2  one thread per face: the traces of the two cells at the Q face points, the
+//            local Lax-Friedrichs flux there, and its projection onto the transverse modes
+//              P_b = sum_q w_q psi_b(s_q) [f(uL) + f(uR) - alpha (uR - uL)],  b = 0..N,
+//            stored in planes [v*(N+1) + b][face] (x faces and y faces apart);
+//   k_cell2  one thread per cell: the volume term, the lifting of the four faces' P_b
+//            and the stage combination.
+// Every face flux is computed once; all lanes of every warp do the same work.
+
+// Values at the Q Gauss points of sum_t e_t psi_t(s).  The points are symmetric
+// (s_{Q-1-q} = -s_q) and psi_t has the parity of t, so the even and odd sums are formed
+// once per pair of points; psi_0 is constant.
+template <int N>
+__device__ __forceinline__ void eval_gauss(const double (&e)[N + 1], double (&out)[N + 1]) {
+  using O = Off<N>;
+  constexpr int Q = N + 1;
+  const double p0 = e[0] * T(O::PQ);
+#pragma unroll
+  for (int q = 0; q < Q / 2; ++q) {
+    double ev = p0, od = e[1] * T(O::PQ + q * (N + 1) + 1);
+#pragma unroll
+    for (int t = 2; t <= N; ++t) {
+      if (t & 1) od = fma(e[t], T(O::PQ + q * (N + 1) + t), od);
+      else ev = fma(e[t], T(O::PQ + q * (N + 1) + t), ev);
+    }
+    out[q] = ev + od;
+    out[Q - 1 - q] = ev - od;
+  }
+  if constexpr (Q & 1) {
+    double ev = p0;
+#pragma unroll
+    for (int t = 2; t <= N; t += 2) ev = fma(e[t], T(O::PQ + (Q / 2) * (N + 1) + t), ev);
+    out[Q / 2] = ev;
+  }
+}
+
+// Trace of a cell on its face normal to `dir` at the Q face points: the +1 side
+// (east / north) or, with minus = true, the -1 side (west / south), whose normal modes of
+// odd degree enter with the opposite sign.  The mirror image of a cell (outflow ghost)
+// therefore gives a bitwise identical trace on the shared face.
+template <int N, int V, int NP>
+__device__ __forceinline__ void face_trace(const double (&u)[V][NP], int dir, bool minus, double (&tr)[N + 1][V]) {
+  using O = Off<N>;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double e[N + 1], val[N + 1];
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {  // transverse degree t, normal degree n
+      double s = u[v][dir == 0 ? mode_idx(0, t) : mode_idx(t, 0)] * T(O::P1);
+#pragma unroll
+      for (int n = 1; n <= N - t; ++n) {
+        const double x = u[v][dir == 0 ? mode_idx(n, t) : mode_idx(t, n)];
+        s = fma((minus && (n & 1)) ? -x : x, T(O::P1 + n), s);
+      }
+      e[t] = s;
+    }
+    eval_gauss<N>(e, val);
+#pragma unroll
+    for (int q = 0; q <= N; ++q) tr[q][v] = val[q];
+  }
+}
+
+// Face tiles: 32 faces along x by 4 rows; Tile::pad = 0 for x faces (k = 0..nx, j < ny),
+// 1 for y faces (k < nx, j = 0..ny).  Face k of a row lies between cells k-1 and k.
+template <int PDE, int N>
+__global__ void __launch_bounds__(128) k_face2(const double* __restrict__ us, const Inst* __restrict__ insts,
+                                               const Tile* __restrict__ tiles, long long ctot, int bc, double gam,
+                                               double* __restrict__ fx, long long fxt, double* __restrict__ fy,
+                                               long long fyt) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1;
+  const Tile tile = tiles[blockIdx.x];
+  const Inst I = insts[tile.inst];
+  const int dir = tile.pad;
+  const int k = tile.x0 + (threadIdx.x & 31), j = tile.y0 + (threadIdx.x >> 5);
+  if (dir == 0 ? (k > I.nx || j >= I.ny) : (k >= I.nx || j > I.ny)) return;
+  const double gm1 = gam - 1.0;
+  double tL[Q][V], tR[Q][V];
+  {
+    double u[V][NP];
+    load_cell<V, NP>(us, ctot, I, dir == 0 ? k - 1 : k, dir == 0 ? j : j - 1, bc, u);
+    face_trace<N>(u, dir, false, tL);
+  }
+  {
+    double u[V][NP];
+    load_cell<V, NP>(us, ctot, I, k, j, bc, u);
+    face_trace<N>(u, dir, true, tR);
+  }
+  double G[Q][V];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) llf_sum<2, PDE>(dir, tL[q], tR[q], G[q], gam, gm1);
+  // P_b = sum_q w_q psi_b(s_q) G(q), summed over symmetric pairs of points
+  double* const base = dir == 0 ? fx + I.fx + (long long)j * (I.nx + 1) + k : fy + I.fy + (long long)j * I.nx + k;
+  const long long stride = dir == 0 ? fxt : fyt;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double S[Q / 2 + 1], D[Q / 2 + 1];
+#pragma unroll
+    for (int q = 0; q < Q / 2; ++q) {
+      S[q] = G[q][v] + G[Q - 1 - q][v];
+      D[q] = G[q][v] - G[Q - 1 - q][v];
+    }
+#pragma unroll
+    for (int b = 0; b <= N; ++b) {
+      double P = 0.0;
+      bool first = true;
+#pragma unroll
+      for (int q = 0; q < Q / 2; ++q) {
+        const double x = (b & 1) ? D[q] : S[q];
+        P = first ? x * T(O::WPQ + q * (N + 1) + b) : fma(x, T(O::WPQ + q * (N + 1) + b), P);
+        first = false;
+      }
+      if ((Q & 1) && !(b & 1)) P = fma(G[Q / 2][v], T(O::WPQ + (Q / 2) * (N + 1) + b), P);
+      base[(long long)(v * (N + 1) + b) * stride] = P;
+    }
+  }
+}
+
+// One thread per cell over the 32 x 8 cell tiles (lane = column, warp = row).
+template <int PDE, int N>
+__global__ void __launch_bounds__(256) k_cell2(const double* __restrict__ un, const double* __restrict__ us,
+                                               double* __restrict__ out, const Inst* __restrict__ insts,
+                                               const Tile* __restrict__ tiles, long long ctot, int stage,
+                                               double dt_all, const double* __restrict__ fx, long long fxt,
+                                               const double* __restrict__ fy, long long fyt, double gam) {
+  using O = Off<N>;
+  constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1;
+  const Tile tile = tiles[blockIdx.x];
+  const Inst I = insts[tile.inst];
+  const int ix = tile.x0 + (threadIdx.x & 31), iy = tile.y0 + (threadIdx.x >> 5);
+  if (ix >= I.nx || iy >= I.ny) return;
+  const long long g = I.off + (long long)iy * I.nx + ix;
+  const double gm1 = gam - 1.0;
+  double u[V][NP];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) u[v][m] = __ldg(us + (long long)(v * NP + m) * ctot + g);
+  // volume term, unscaled: X_ab = sum_q w w f psi_a' psi_b (a >= 1), Y_ab likewise with g (b >= 1)
+  double X[V][NP], Y[V][NP];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) X[v][m] = Y[v][m] = 0.0;
+#pragma unroll
+  for (int qx = 0; qx < Q; ++qx) {
+    double tb[V][N + 1];
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int b = 0; b <= N; ++b) {
+        double t = u[v][mode_idx(0, b)] * T(O::PQ + qx * (N + 1));
+#pragma unroll
+        for (int a = 1; a <= N - b; ++a) t = fma(u[v][mode_idx(a, b)], T(O::PQ + qx * (N + 1) + a), t);
+        tb[v][b] = t;
+      }
+    double col[V][Q];  // u at (x_qx, y_qy) for every qy
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      double val[Q];
+      eval_gauss<N>(tb[v], val);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
+    }
+#pragma unroll
+    for (int qy = 0; qy < Q; ++qy) {
+      const int q = qy * Q + qx;
+      double f[V], gg[V];
+      if constexpr (PDE == 0) {
+        const double h = 0.5 * col[0][qy] * col[0][qy];
+        f[0] = h;
+        gg[0] = h;
+      } else {
+        const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
+        const double r = 1.0 / rho;
+        const double vx = mx * r, vy = my * r;
+        const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
+        const double ep = E + p;
+        f[0] = mx;
+        f[1] = fma(mx, vx, p);
+        f[2] = my * vx;
+        f[3] = ep * vx;
+        gg[0] = my;
+        gg[1] = f[2];
+        gg[2] = fma(my, vy, p);
+        gg[3] = ep * vy;
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int m = 1; m < NP; ++m) {
+          if (mode_a(m) >= 1) X[v][m] = fma(f[v], T(O::VDX + q * NP + m), X[v][m]);
+          if (mode_b(m) >= 1) Y[v][m] = fma(gg[v], T(O::VDY + q * NP + m), Y[v][m]);
+        }
+    }
+  }
+  // acc = (2/hx) X + (2/hy) Y - (1/hx) psi_a(1) [P_b(E) -+ P_b(W)] - (1/hy) psi_b(1) [P_a(N) -+ P_a(S)]
+  const double sx = 2.0 / I.hx, sy = 2.0 / I.hy, ihx = 0.5 * sx, ihy = 0.5 * sy;
+  double cx[N + 1], cy[N + 1];
+#pragma unroll
+  for (int n = 0; n <= N; ++n) {
+    cx[n] = -ihx * T(O::P1 + n);
+    cy[n] = -ihy * T(O::P1 + n);
+  }
+  const double* const pw = fx + I.fx + (long long)iy * (I.nx + 1) + ix;  // west face; east = pw + 1
+  const double* const ps = fy + I.fy + (long long)iy * I.nx + ix;        // south face; north = ps + nx
+  const double dt = dt_all > 0.0 ? dt_all : I.dt;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double acc[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      const bool hx_ = mode_a(m) >= 1, hy_ = mode_b(m) >= 1;
+      acc[m] = hx_ ? (hy_ ? fma(sx, X[v][m], sy * Y[v][m]) : sx * X[v][m]) : (hy_ ? sy * Y[v][m] : 0.0);
+    }
+#pragma unroll
+    for (int b = 0; b <= N; ++b) {
+      const long long pl = (long long)(v * (N + 1) + b);
+      const double PW = __ldg(pw + pl * fxt), PE = __ldg(pw + pl * fxt + 1);
+      const double PS = __ldg(ps + pl * fyt), PN = __ldg(ps + pl * fyt + I.nx);
+      const double Dx = PE - PW, Sx = PE + PW, Dy = PN - PS, Sy = PN + PS;
+#pragma unroll
+      for (int a = 0; a <= N - b; ++a) {
+        const int mx = mode_idx(a, b);  // x faces: normal degree a, transverse degree b
+        acc[mx] = fma(cx[a], (a & 1) ? Sx : Dx, acc[mx]);
+        const int my = mode_idx(b, a);  // y faces: transverse degree b (in x), normal a
+        acc[my] = fma(cy[a], (a & 1) ? Sy : Dy, acc[my]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      const long long idx = (long long)(v * NP + m) * ctot + g;
+      const double e = fma(dt, acc[m], us[idx]);
+      double r;
+      if (stage == 1) r = e;
+      else if (stage == 2) r = fma(0.75, un[idx], 0.25 * e);
+      else r = fma(1.0 / 3.0, un[idx], (2.0 / 3.0) * e);
+      out[idx] = r;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- indicator
 // TVB modified minmod (Cockburn-Shu) on conserved variables, x test on the east/west
 // edge midpoints and y test on the north/south ones.  The face values and means are
@@ -1079,6 +1322,14 @@ static void run_stage2(const LaunchArgs& a, int stage, double dt_all, int* queue
   const size_t bytes = stage_smem2<PDE, N, TYS>();
   k2::k_stage2<PDE, N, TYS><<<queue ? grid : a.ntiles, (TYS + 3) * 32, bytes, a.st>>>(
       a.un, a.us, a.out, a.inst, a.tiles, a.ctot, a.bc, stage, dt_all, a.gam, a.ntiles, queue);
+}
+// split form: the face pass over the face tiles, then the cell pass over the 32 x 8 cell tiles
+void launch_stage2_split(int pde, int N, const LaunchArgs& a, int stage, double dt_all, const Tile* face_tiles,
+                         int nface_tiles, double* fx, long long fxt, double* fy, long long fyt) {
+  DG_DISPATCH2(pde, N, (k2::k_face2<P_, N_><<<nface_tiles, 128, 0, a.st>>>(a.us, a.inst, face_tiles, a.ctot, a.bc,
+                                                                            a.gam, fx, fxt, fy, fyt)));
+  DG_DISPATCH2(pde, N, (k2::k_cell2<P_, N_><<<a.ntiles, 256, 0, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
+                                                                         stage, dt_all, fx, fxt, fy, fyt, a.gam)));
 }
 int tile_w2() { return k2::TX; }
 int tile_h2() { return k2::TY; }

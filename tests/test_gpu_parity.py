@@ -338,4 +338,4 @@ def test_call_order_errors_and_launch_count():
         before = g.launches
         g.step(1e-4)
     torch.cuda.synchronize()
-    assert g.launches - before == 15  # 3 x (stage, flags, limiter, scatter, statistics)
+    assert g.launches - before == 18  # 3 x (face and cell passes, flags, limiter, scatter, statistics)

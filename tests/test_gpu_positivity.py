@@ -99,7 +99,7 @@ def test_step_with_scaling_quadrant_p3():
     g.step(dt)
     g.set_positivity(False)
     g.step(dt)
-    assert g.launches - before == 2 * 15 + 3
+    assert g.launches - before == 2 * 18 + 3
 
 
 @pytest.mark.parametrize("dim,N", [(1, 2), (1, 3), (2, 2), (2, 3)])
