@@ -31,7 +31,8 @@ struct Lay {
   static constexpr int SIZE_LIM = NS * N1 + N1 * NG * N1 + NG * N1 + N1 * N1 * N1 + NG * N1 + NG +
                                   2 * NG * N1 + 3 * NG;
   static constexpr int SIZE_PROJ = 3 * 8 + 8 * N1;
-  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ;
+  static constexpr int SIZE_SPLIT = Q * N1;
+  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT;
 };
 __host__ __device__ constexpr int base_of(int N) {
   return N == 1 ? 0 : (N == 2 ? Lay<1>::SIZE : Lay<1>::SIZE + Lay<2>::SIZE);
@@ -66,7 +67,8 @@ struct Off {
   static constexpr int PW = PX + 8;              // [8]
   static constexpr int PQP = PW + 8;             // [8] (count in slot 0)
   static constexpr int PP = PQP + 8;             // [8][N1]
-  static constexpr int END = PP + 8 * N1;
+  static constexpr int WDQ = PP + 8 * N1;        // [Q][N1] w_q psi_n'(x_q)
+  static constexpr int END = WDQ + Q * N1;
 };
 static_assert(Off<3>::END == Lay<1>::SIZE + Lay<2>::SIZE + Lay<3>::SIZE, "table layout");
 constexpr int kTabSize = Off<3>::END;
@@ -129,6 +131,8 @@ void pack(const dgt::Tabs& t, double* h) {
     for (int n = 0; n < N1; ++n) h[O::PP + q * N1 + n] = t.ppsi[q][n];
   }
   h[O::PQP] = t.QP;
+  for (int q = 0; q < Q; ++q)
+    for (int n = 0; n < N1; ++n) h[O::WDQ + q * N1 + n] = t.gw[q] * t.dpsi_q[q][n];
 }
 
 // ----------------------------------------------------------------------------- loads
@@ -617,8 +621,9 @@ __global__ void __launch_bounds__(128) k_face2(const double* __restrict__ us, co
 }
 
 // One thread per cell over the 32 x 8 cell tiles (lane = column, warp = row).
+// Two blocks per SM (at most 128 registers) except for Euler P3, which needs more registers.
 template <int PDE, int N>
-__global__ void __launch_bounds__(256) k_cell2(const double* __restrict__ un, const double* __restrict__ us,
+__global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(const double* __restrict__ un, const double* __restrict__ us,
                                                double* __restrict__ out, const Inst* __restrict__ insts,
                                                const Tile* __restrict__ tiles, long long ctot, int stage,
                                                double dt_all, const double* __restrict__ fx, long long fxt,
@@ -636,62 +641,164 @@ __global__ void __launch_bounds__(256) k_cell2(const double* __restrict__ un, co
   for (int v = 0; v < V; ++v)
 #pragma unroll
     for (int m = 0; m < NP; ++m) u[v][m] = __ldg(us + (long long)(v * NP + m) * ctot + g);
-  // volume term, unscaled: X_ab = sum_q w w f psi_a' psi_b (a >= 1), Y_ab likewise with g (b >= 1)
+  // volume term, unscaled: X_ab = sum_q w w f psi_a' psi_b (a >= 1), Y_ab likewise with g (b >= 1),
+  // sum-factorised: for every x point the column sums over y, then the x weights
   double X[V][NP], Y[V][NP];
 #pragma unroll
   for (int v = 0; v < V; ++v)
 #pragma unroll
     for (int m = 0; m < NP; ++m) X[v][m] = Y[v][m] = 0.0;
+  if constexpr (PDE == 1 && N == 3) {
 #pragma unroll
-  for (int qx = 0; qx < Q; ++qx) {
-    double tb[V][N + 1];
+    for (int qx = 0; qx < Q; ++qx) {
+      double tb[V][N + 1];
 #pragma unroll
-    for (int v = 0; v < V; ++v)
+      for (int v = 0; v < V; ++v)
 #pragma unroll
-      for (int b = 0; b <= N; ++b) {
-        double t = u[v][mode_idx(0, b)] * T(O::PQ + qx * (N + 1));
+        for (int b = 0; b <= N; ++b) {
+          double t = u[v][mode_idx(0, b)] * T(O::PQ + qx * (N + 1));
 #pragma unroll
-        for (int a = 1; a <= N - b; ++a) t = fma(u[v][mode_idx(a, b)], T(O::PQ + qx * (N + 1) + a), t);
-        tb[v][b] = t;
+          for (int a = 1; a <= N - b; ++a) t = fma(u[v][mode_idx(a, b)], T(O::PQ + qx * (N + 1) + a), t);
+          tb[v][b] = t;
+        }
+      double col[V][Q];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double val[Q];
+        eval_gauss<N>(tb[v], val);
+#pragma unroll
+        for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
       }
-    double col[V][Q];  // u at (x_qx, y_qy) for every qy
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      double val[Q];
-      eval_gauss<N>(tb[v], val);
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
-    }
-#pragma unroll
-    for (int qy = 0; qy < Q; ++qy) {
-      const int q = qy * Q + qx;
-      double f[V], gg[V];
-      if constexpr (PDE == 0) {
-        const double h = 0.5 * col[0][qy] * col[0][qy];
-        f[0] = h;
-        gg[0] = h;
-      } else {
+      for (int qy = 0; qy < Q; ++qy) {
+        const int q = qy * Q + qx;
         const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
         const double r = 1.0 / rho;
         const double vx = mx * r, vy = my * r;
         const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
         const double ep = E + p;
-        f[0] = mx;
-        f[1] = fma(mx, vx, p);
-        f[2] = my * vx;
-        f[3] = ep * vx;
-        gg[0] = my;
-        gg[1] = f[2];
-        gg[2] = fma(my, vy, p);
-        gg[3] = ep * vy;
+        const double f[V] = {mx, fma(mx, vx, p), my * vx, ep * vx};
+        const double gg[V] = {my, f[2], fma(my, vy, p), ep * vy};
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+          for (int m = 1; m < NP; ++m) {
+            if (mode_a(m) >= 1) X[v][m] = fma(f[v], T(O::VDX + q * NP + m), X[v][m]);
+            if (mode_b(m) >= 1) Y[v][m] = fma(gg[v], T(O::VDY + q * NP + m), Y[v][m]);
+          }
       }
-#pragma unroll
+    }
+  } else {
+    // x points in symmetric pairs (t_b formed once per pair).  Euler P3 takes the direct
+    // form (one quadrature point at a time), which needs fewer registers.
+    constexpr bool kPair = true;
+    constexpr int NX = (Q + 1) / 2;
+  #pragma unroll
+    for (int qp = 0; qp < NX; ++qp) {
+      // t_b(x) = sum_a U_ab psi_a(x) at the pair of points x_qp and x_{Q-1-qp} = -x_qp (parts
+      // even and odd in a), or at one point (for the middle point 0, psi_a vanishes for odd a)
+      const bool single = !kPair || ((Q & 1) && qp == Q / 2);
+      const bool zero = (Q & 1) && qp == Q / 2;
+      double tb[2][V][N + 1];
+  #pragma unroll
       for (int v = 0; v < V; ++v)
-#pragma unroll
-        for (int m = 1; m < NP; ++m) {
-          if (mode_a(m) >= 1) X[v][m] = fma(f[v], T(O::VDX + q * NP + m), X[v][m]);
-          if (mode_b(m) >= 1) Y[v][m] = fma(gg[v], T(O::VDY + q * NP + m), Y[v][m]);
+  #pragma unroll
+        for (int b = 0; b <= N; ++b) {
+          double ev = u[v][mode_idx(0, b)] * T(O::PQ + qp * (N + 1)), od = 0.0;
+  #pragma unroll
+          for (int a = 1; a <= N - b; ++a) {
+            if (a & 1) {
+              if (zero) continue;
+              if (single) ev = fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), ev);
+              else od = a == 1 ? u[v][mode_idx(a, b)] * T(O::PQ + qp * (N + 1) + a)
+                               : fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), od);
+            } else {
+              ev = fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), ev);
+            }
+          }
+          const bool has_od = !single && b < N;
+          tb[0][v][b] = has_od ? ev + od : ev;
+          tb[1][v][b] = has_od ? ev - od : ev;
         }
+  #pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        if (single && side == 1) break;
+        const int qx = side == 0 ? qp : Q - 1 - qp;
+        const bool mid = (Q & 1) && qx == Q / 2;
+        double col[V][Q];  // u at (x_qx, y_qy) for every qy
+  #pragma unroll
+        for (int v = 0; v < V; ++v) {
+          double val[Q];
+          eval_gauss<N>(tb[side][v], val);
+  #pragma unroll
+          for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
+        }
+        double F[Q][V], Gq[Q][V];
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          if constexpr (PDE == 0) {
+            const double h = 0.5 * col[0][qy] * col[0][qy];
+            F[qy][0] = h;
+            Gq[qy][0] = h;
+          } else {
+            const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
+            const double r = 1.0 / rho;
+            const double vx = mx * r, vy = my * r;
+            const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
+            const double ep = E + p;
+            F[qy][0] = mx;
+            F[qy][1] = fma(mx, vx, p);
+            F[qy][2] = my * vx;
+            F[qy][3] = ep * vx;
+            Gq[qy][0] = my;
+            Gq[qy][1] = F[qy][2];
+            Gq[qy][2] = fma(my, vy, p);
+            Gq[qy][3] = ep * vy;
+          }
+        }
+  #pragma unroll
+        for (int v = 0; v < V; ++v) {
+          // sums and differences over the symmetric pairs of y points
+          double fS[Q / 2 + 1], fD[Q / 2 + 1], gS[Q / 2 + 1], gD[Q / 2 + 1];
+  #pragma unroll
+          for (int q = 0; q < Q / 2; ++q) {
+            fS[q] = F[q][v] + F[Q - 1 - q][v];
+            fD[q] = F[q][v] - F[Q - 1 - q][v];
+            gS[q] = Gq[q][v] + Gq[Q - 1 - q][v];
+            gD[q] = Gq[q][v] - Gq[Q - 1 - q][v];
+          }
+          // x derivative part: G_b = sum_y w psi_b(y) f (psi_b has the parity of b)
+  #pragma unroll
+          for (int b = 0; b < N; ++b) {
+            double G = 0.0;
+  #pragma unroll
+            for (int q = 0; q < Q / 2; ++q)
+              G = q == 0 ? ((b & 1) ? fD[0] : fS[0]) * T(O::WPQ + b)
+                         : fma((b & 1) ? fD[q] : fS[q], T(O::WPQ + q * (N + 1) + b), G);
+            if ((Q & 1) && !(b & 1)) G = fma(F[Q / 2][v], T(O::WPQ + (Q / 2) * (N + 1) + b), G);
+  #pragma unroll
+            for (int a = 1; a <= N - b; ++a) {
+              if (mid && !(a & 1)) continue;  // psi_a'(0) = 0 for even a
+              X[v][mode_idx(a, b)] = fma(T(O::WDQ + qx * (N + 1) + a), G, X[v][mode_idx(a, b)]);
+            }
+          }
+          // y derivative part: H_b = sum_y w psi_b'(y) g (psi_b' has the parity of b + 1)
+  #pragma unroll
+          for (int b = 1; b <= N; ++b) {
+            double H = 0.0;
+  #pragma unroll
+            for (int q = 0; q < Q / 2; ++q)
+              H = q == 0 ? ((b & 1) ? gS[0] : gD[0]) * T(O::WDQ + b)
+                         : fma((b & 1) ? gS[q] : gD[q], T(O::WDQ + q * (N + 1) + b), H);
+            if ((Q & 1) && (b & 1)) H = fma(Gq[Q / 2][v], T(O::WDQ + (Q / 2) * (N + 1) + b), H);
+  #pragma unroll
+            for (int a = 0; a <= N - b; ++a) {
+              if (mid && (a & 1)) continue;  // psi_a(0) = 0 for odd a
+              Y[v][mode_idx(a, b)] = fma(T(O::WPQ + qx * (N + 1) + a), H, Y[v][mode_idx(a, b)]);
+            }
+          }
+        }
+      }
     }
   }
   // acc = (2/hx) X + (2/hy) Y - (1/hx) psi_a(1) [P_b(E) -+ P_b(W)] - (1/hy) psi_b(1) [P_a(N) -+ P_a(S)]
