@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
       for (int qy = 0; qy < Q; ++qy) {
         const int q = qy * Q + qx;
         const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
-        const double r = 1.0 / rho;
+        const double r = rcp_d(rho);
         const double vx = mx * r, vy = my * r;
         const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
         const double ep = E + p;
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
             Gq[qy][0] = h;
           } else {
             const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
-            const double r = 1.0 / rho;
+            const double r = rcp_d(rho);
             const double vx = mx * r, vy = my * r;
             const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
             const double ep = E + p;
