@@ -33,30 +33,70 @@ from paper_1904_11147_gb300 import workloads as W  # noqa: E402
 
 METRIC = "2D Euler P2 DG DOF-updates/s incl. CSWENO; learned vs plain indicator"
 UNIT = "DOF-updates/s"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector) nominal; the measured value is used when present
+# GB300 FP64 vector peak from unit counts and clock: 2 DFMA lanes per clock per SM x 2 flops
+# x 152 SMs x 2.07 GHz (MEASURED_PEAKS.json carries no FP64 figure)
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
 # ----------------------------------------------------------------------------- algorithmic work
-def stage_flops_per_cell(dim: int, pde: int, N: int) -> int:
-    """FP64 flops of one stage of Eq. (5) for one cell, counted from the formulation the
-    stage kernel evaluates (FMA = 2, add/mul/div/sqrt = 1); halo work is not counted."""
+def stage_flops_per_cell(dim: int, pde: int, N: int, faces_per_cell: float = 2.0) -> dict:
+    """FP64 flops of one stage of Eq. (5) per cell, counted from the operations the split
+    stage evaluates (FMA = 2; add, multiply, reciprocal, square root = 1): the face pass
+    (two traces, the local Lax-Friedrichs flux at the N+1 face points, the projection on the
+    transverse modes) for `faces_per_cell` faces, and the cell pass (sum-factorised volume
+    term over symmetric Gauss pairs, lifting, stage combination averaged over the three
+    stages)."""
     assert dim == 2
     V = 1 if pde == 0 else 4
     NP = (N + 1) * (N + 2) // 2
     Q = N + 1
+    pairs, mid = Q // 2, Q % 2
+    even = lambda lo, hi: sum(1 for t in range(lo, hi + 1) if t % 2 == 0)
+    odd = lambda lo, hi: sum(1 for t in range(lo, hi + 1) if t % 2 == 1)
+
+    def eval_gauss():  # values of sum_t e_t psi_t at the Q Gauss points
+        per_pair = (1 + 2 * odd(3, N)) + 2 * even(2, N) + 2
+        return 1 + pairs * per_pair + mid * 2 * even(2, N)
+
+    flux = 18 if pde == 1 else 2  # one state's flux and wave speed
+    # face pass, per face
+    trace = V * (sum(1 + 2 * (N - t) for t in range(N + 1)) + eval_gauss())
+    llf = 2 * flux + 1 + 4 * V
+    proj = V * (2 * pairs + sum(1 + 2 * (pairs - 1) + (2 if (mid and b % 2 == 0) else 0) for b in range(N + 1)))
+    face = 2 * trace + Q * llf + proj
+    # cell pass, per cell
+    vflux = 18 if pde == 1 else 2
+    if pde == 1 and N == 3:  # direct form: t_b per x point, products at every point
+        ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
+        tb = Q * V * sum(1 + 2 * (N - b) for b in range(N + 1))
+        cols = Q * V * eval_gauss()
+        red = Q * Q * V * 2 * (sum(1 for a, b in ab if a >= 1) + sum(1 for a, b in ab if b >= 1))
+    else:
+        tb = 0
+        for qp in range((Q + 1) // 2):
+            single = mid and qp == Q // 2
+            for b in range(N + 1):
+                tb += V * (1 + 2 * even(2, N - b))
+                if not single and N - b >= 1:
+                    tb += V * (1 + 2 * odd(3, N - b) + 2)
+        cols = Q * V * eval_gauss()
+        red = 0
+        for qx in range(Q):
+            is_mid = mid and qx == Q // 2
+            r = 4 * pairs  # sums and differences of f and g over the y pairs
+            for b in range(N):  # x-derivative column sums and their x weights
+                r += 1 + 2 * (pairs - 1) + (2 if (mid and b % 2 == 0) else 0)
+                r += 2 * sum(1 for a in range(1, N - b + 1) if not (is_mid and a % 2 == 0))
+            for b in range(1, N + 1):  # y-derivative column sums
+                r += 1 + 2 * (pairs - 1) + (2 if (mid and b % 2 == 1) else 0)
+                r += 2 * sum(1 for a in range(0, N - b + 1) if not (is_mid and a % 2 == 1))
+            red += V * r
     ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
-    n_dx = sum(1 for a, b in ab if a >= 1)
-    n_dy = sum(1 for a, b in ab if b >= 1)
-    # sum-factorised evaluation: t_b(x) for every x point, then u at every (x, y) point
-    evalf = Q * V * (N + 1) ** 2 + Q * Q * V * (2 * (N + 1) - 1)
-    flux = Q * Q * (24 if pde == 1 else 4)
-    proj = Q * Q * V * 2 * (n_dx + n_dy)
-    traces = 2 * V * (2 * NP + 2 * (N + 1) + Q * (N + 1) * 4)
-    llf_point = (57 if pde == 1 else 3 * 2 + 1 + 5)
-    llf = 2 * Q * llf_point
-    lift = V * (4 * Q + 4 * (N + 1) * Q * 2 + 2 * NP * 2)
-    rk = V * NP * 4
-    return evalf + flux + proj + traces + llf + lift + rk
+    combine = V * sum((3 if (a >= 1 and b >= 1) else 1) for a, b in ab if a >= 1 or b >= 1) + 4 + 2 * (N + 1) + 2
+    lift = V * (4 * (N + 1) + 4 * NP)
+    rk = V * NP * (2 + 5 + 5) / 3.0
+    cell = tb + cols + Q * Q * vflux + red + combine + lift + rk
+    return {"face": face, "cell": cell, "total": faces_per_cell * face + cell}
 
 
 def measured_peaks():
@@ -392,9 +432,11 @@ def main():
     if rank != 0:
         return 0
     peaks, src = measured_peaks()
-    fp64_peak = float(peaks.get("fp64_tflops", FP64_NOMINAL_TFLOPS))
-    peak_note = "FP64 nominal 1.25 TFLOP/s (2 DFMA/clk/SM x 152 SMs x 2.07 GHz); microbenchmark on this pool: 1.20"
-    flops_cell = stage_flops_per_cell(2, 1, 2)
+    fp64_peak = float(peaks.get("fp64_tflops", FP64_PEAK_TFLOPS))
+    peak_note = ("FP64 from unit counts and clock: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = %.3f TFLOP/s "
+                 "(an FMA microbenchmark on this pool reached 1.20)" % FP64_PEAK_TFLOPS)
+    fl = stage_flops_per_cell(2, 1, 2, faces_per_cell=((n + 1) * n * 2) / (n * n))
+    flops_cell = fl["total"]
     achieved = flops_cell * n * n / (stage_ms / 1e3) / 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "stage_traffic.json")
@@ -407,7 +449,7 @@ def main():
             traffic = None
     cpu_line = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(n, dt, win=48, steps=6)
+        rate, cores, sample = cpu_oracle_rate(n, dt, win=64, steps=24)
         cpu_line = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -429,9 +471,11 @@ def main():
         "learned_over_plain": value / value_plain,
         "kxrcf": kx,
         "parent_weno": pw,
-        "roofline": {"bound": "alu", "kernel": "k_stage2<Euler,P2>", "achieved": achieved, "peak": fp64_peak,
+        "roofline": {"bound": "alu", "kernel": "k_face2 + k_cell2 <Euler,P2> (one stage)", "achieved": achieved,
+                     "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
-                     "flops_per_cell": flops_cell, "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},
+                     "flops_per_cell": flops_cell, "flops_per_face": fl["face"], "flops_cell_pass": fl["cell"],
+                     "launch_ms": stage_ms, "peak_source": src if "fp64_tflops" in peaks else peak_note},
         "hbm_fraction": dofs * 64 / (ms / args.steps / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
         "hbm_peak_source": "measured" if "hbm_gbs" in peaks else "fallback 6800 GB/s",
         "cpu_baseline": cpu_line,

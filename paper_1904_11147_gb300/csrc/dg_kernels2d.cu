@@ -32,7 +32,8 @@ struct Lay {
                                   2 * NG * N1 + 3 * NG;
   static constexpr int SIZE_PROJ = 3 * 8 + 8 * N1;
   static constexpr int SIZE_SPLIT = Q * N1;
-  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT;
+  static constexpr int SIZE_LIM2 = N1 * (N1 * (N1 + 1) / 2) + NG * N1;
+  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT + SIZE_LIM2;
 };
 __host__ __device__ constexpr int base_of(int N) {
   return N == 1 ? 0 : (N == 2 ? Lay<1>::SIZE : Lay<1>::SIZE + Lay<2>::SIZE);
@@ -68,7 +69,9 @@ struct Off {
   static constexpr int PQP = PW + 8;             // [8] (count in slot 0)
   static constexpr int PP = PQP + 8;             // [8][N1]
   static constexpr int WDQ = PP + 8 * N1;        // [Q][N1] w_q psi_n'(x_q)
-  static constexpr int END = WDQ + Q * N1;
+  static constexpr int BS = WDQ + Q * N1;        // [N1][k <= l] B_kk, B_kl + B_lk
+  static constexpr int WPG = BS + N1 * (N1 * (N1 + 1) / 2);  // [NG][N1] w_g psi_n(r_g)
+  static constexpr int END = WPG + NG * N1;
 };
 static_assert(Off<3>::END == Lay<1>::SIZE + Lay<2>::SIZE + Lay<3>::SIZE, "table layout");
 constexpr int kTabSize = Off<3>::END;
@@ -133,6 +136,13 @@ void pack(const dgt::Tabs& t, double* h) {
   h[O::PQP] = t.QP;
   for (int q = 0; q < Q; ++q)
     for (int n = 0; n < N1; ++n) h[O::WDQ + q * N1 + n] = t.gw[q] * t.dpsi_q[q][n];
+  for (int i = 0; i < N1; ++i) {
+    int j = 0;
+    for (int k = 0; k < N1; ++k)
+      for (int l = k; l < N1; ++l, ++j) h[O::BS + i * (N1 * (N1 + 1) / 2) + j] = k == l ? t.B[i][k][k] : t.B[i][k][l] + t.B[i][l][k];
+  }
+  for (int g = 0; g < NG; ++g)
+    for (int n = 0; n < N1; ++n) h[O::WPG + g * N1 + n] = t.rw[g] * t.psiG[g][n];
 }
 
 // ----------------------------------------------------------------------------- loads
@@ -927,7 +937,7 @@ __global__ void __launch_bounds__(256)
 template <int N>
 __device__ __forceinline__ void weno(const double* avg, double* out) {
   using O = Off<N>;
-  constexpr int N1 = N + 1, NG = O::NG;
+  constexpr int N1 = N + 1, NG = O::NG, NB = N1 * (N1 + 1) / 2;
   const double eps = 1e-6;
   // beta_i and p_i - c do not change when a constant c is removed from all averages
   // (constants are reproduced; Eq. (13) holds only derivatives): work on averages
@@ -936,29 +946,34 @@ __device__ __forceinline__ void weno(const double* avg, double* out) {
   double dv[2 * N + 1];
 #pragma unroll
   for (int k = 0; k < 2 * N + 1; ++k) dv[k] = avg[k] - c;
+  // Eq. (13) as a symmetric quadratic form: beta_i = sum_k dv_k sum_{l >= k} Bs_kl dv_l;
+  // inv_i = 1 / (eps + beta_i)^2
   double inv[N1];
 #pragma unroll
   for (int i = 0; i < N1; ++i) {
     double beta = 0.0;
+    int j = 0;
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
-      double r = 0.0;
+      double r = T(O::BS + i * NB + j) * dv[i + k];
+      ++j;
 #pragma unroll
-      for (int l = 0; l < N1; ++l) r = fma(T(O::BB + (i * N1 + k) * N1 + l), dv[i + l], r);
-      beta = fma(dv[i + k], r, beta);
+      for (int l = k + 1; l < N1; ++l, ++j) r = fma(T(O::BS + i * NB + j), dv[i + l], r);
+      beta = k == 0 ? dv[i] * r : fma(dv[i + k], r, beta);
     }
     const double d = eps + beta;
-    inv[i] = 1.0 / (d * d);
+    inv[i] = rcp_d(d * d);
   }
+  // Eqs. (14)-(15): u_g = c + sum_i wbar_i (p_i - c) / sum_i wbar_i
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     double p[N1];
 #pragma unroll
     for (int i = 0; i < N1; ++i) {
-      double s = 0.0;
+      double s = T(O::WC + (i * NG + g) * N1) * dv[i];
 #pragma unroll
-      for (int k = 0; k < N1; ++k) s = fma(T(O::WC + (i * NG + g) * N1 + k), dv[i + k], s);
-      p[i] = c + s;
+      for (int k = 1; k < N1; ++k) s = fma(T(O::WC + (i * NG + g) * N1 + k), dv[i + k], s);
+      p[i] = s;
     }
     if (T(O::NEG + g) == 0.0) {
       double sw = 0.0, su = 0.0;
@@ -968,7 +983,7 @@ __device__ __forceinline__ void weno(const double* avg, double* out) {
         sw += wb;
         su = fma(wb, p[i], su);
       }
-      out[g] = su / sw;
+      out[g] = fma(su, rcp_d(sw), c);
     } else {
       double swp = 0.0, sup = 0.0, swm = 0.0, sum = 0.0;
 #pragma unroll
@@ -980,7 +995,8 @@ __device__ __forceinline__ void weno(const double* avg, double* out) {
         swm += wm;
         sum = fma(wm, p[i], sum);
       }
-      out[g] = T(O::SGP + g) * (sup / swp) - T(O::SGM + g) * (sum / swm);
+      // sigma+ - sigma- = 1: the constant c passes through the split unchanged
+      out[g] = c + (T(O::SGP + g) * (sup * rcp_d(swp)) - T(O::SGM + g) * (sum * rcp_d(swm)));
     }
   }
 }
@@ -1140,7 +1156,7 @@ __global__ void __launch_bounds__(128)
         for (int a = 0; a <= N; ++a) {
           double s = 0.0;
 #pragma unroll
-          for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WG + gx) * T(O::PG + gx * N1 + a), pv[v][gy][gx], s);
+          for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WPG + gx * N1 + a), pv[v][gy][gx], s);
           tq[gy][a] = s;
         }
 #pragma unroll
@@ -1148,7 +1164,7 @@ __global__ void __launch_bounds__(128)
         const int a = mode_a(m), b = mode_b(m);
         double s = 0.0;
 #pragma unroll
-        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WG + gy) * T(O::PG + gy * N1 + b), tq[gy][a], s);
+        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WPG + gy * N1 + b), tq[gy][a], s);
         lim[(long long)(v * NP + m) * cap + i] = s;
       }
     }
@@ -1293,7 +1309,7 @@ __global__ void __launch_bounds__(128)
       for (int a = 0; a <= N; ++a) {
         double s = 0.0;
 #pragma unroll
-        for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WG + gx) * T(O::PG + gx * N1 + a), pv[gy][gx], s);
+        for (int gx = 0; gx < NG; ++gx) s = fma(T(O::WPG + gx * N1 + a), pv[gy][gx], s);
         tq[gy][a] = s;
       }
     if (active) {
@@ -1302,7 +1318,7 @@ __global__ void __launch_bounds__(128)
         const int a = mode_a(m), b = mode_b(m);
         double s = 0.0;
 #pragma unroll
-        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WG + gy) * T(O::PG + gy * N1 + b), tq[gy][a], s);
+        for (int gy = 0; gy < NG; ++gy) s = fma(T(O::WPG + gy * N1 + b), tq[gy][a], s);
         lim[(long long)(q * NP + m) * cap + i] = s;
       }
     }

@@ -61,8 +61,9 @@ __device__ __forceinline__ void weno_p(const PTab& t, const double* avg, double*
       beta = fma(dv[i + k], r, beta);
     }
     const double d = eps + beta;
-    inv[i] = 1.0 / (d * d);
+    inv[i] = rcp_d(d * d);
   }
+  // u_g = c + sum_i wbar_i (p_i - c) / sum_i wbar_i
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     double p[N1];
@@ -71,7 +72,7 @@ __device__ __forceinline__ void weno_p(const PTab& t, const double* avg, double*
       double s = 0.0;
 #pragma unroll
       for (int k = 0; k < N1; ++k) s = fma(t.C[i][g][k], dv[i + k], s);
-      p[i] = c + s;
+      p[i] = s;
     }
     if (t.neg[g] == 0.0) {
       double sw = 0.0, su = 0.0;
@@ -81,7 +82,7 @@ __device__ __forceinline__ void weno_p(const PTab& t, const double* avg, double*
         sw += wb;
         su = fma(wb, p[i], su);
       }
-      out[g] = su / sw;
+      out[g] = fma(su, rcp_d(sw), c);
     } else {
       double swp = 0.0, sup = 0.0, swm = 0.0, sum = 0.0;
 #pragma unroll
@@ -92,7 +93,8 @@ __device__ __forceinline__ void weno_p(const PTab& t, const double* avg, double*
         swm += wm;
         sum = fma(wm, p[i], sum);
       }
-      out[g] = t.sgp[g] * (sup / swp) - t.sgm[g] * (sum / swm);
+      // sigma+ - sigma- = 1: the constant c passes through the split unchanged
+      out[g] = c + (t.sgp[g] * (sup * rcp_d(swp)) - t.sgm[g] * (sum * rcp_d(swm)));
     }
   }
 }
