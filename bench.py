@@ -292,6 +292,9 @@ def main():
     ap.add_argument("--arms", default="both", choices=["both", "plain"],
                     help="plain: time only the TVB indicator (no training; for profiling runs)")
     ap.add_argument("--clocks-out", default=None)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch configuration (split stage, 8 limiter blocks "
+                         "per SM), e.g. for a profiler run whose timings would mislead the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -331,7 +334,8 @@ def main():
     mesh = make_mesh(False)
     ws = mesh.max_wavespeed()[0]
     dt = 0.1 / (ws[0] * n + ws[1] * n)
-    tune = mesh.autotune(dt)  # stage tile height and limiter grid, measured here (untimed)
+    # stage form and limiter grid, measured here (untimed)
+    tune = (0, 8, 0) if args.no_autotune else mesh.autotune(dt)
     dofs = mesh.size
     u0 = torch.empty(dofs, dtype=torch.float64, device="cuda")
     mesh.get_modes(u0)
@@ -525,7 +529,7 @@ def batched_arm(args, dist, rank, world, torch, dgl):
         hy = (w.box[i][3] - w.box[i][2]) / w.ny[i]
         dts.append(0.1 / (ws[i, 0] / hx + ws[i, 1] / hy))
     m.set_dt(dts)
-    tune = m.autotune(min(dts))
+    tune = (0, 8, 0) if args.no_autotune else m.autotune(min(dts))
     m.set_dt(dts)
     dofs = m.size
 
