@@ -165,6 +165,7 @@ struct dg_mesh {
   int n_stage_tiles = 0;
   int stage_persistent = 0;  // persistent tile queue (1) or one block per tile (0)
   int* d_queue = nullptr;
+  unsigned int* d_lq = nullptr;  // work counter of the 2D Euler limiter
   // split 2D stage (face pass + cell pass; stage_ty == 0): face flux planes, x faces then
   // y faces, with their plane strides, and the face tiles
   bool stage_split = false;
@@ -223,6 +224,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_tiles);
   cudaFree(m->d_stage_tiles);
   cudaFree(m->d_queue);
+  cudaFree(m->d_lq);
   cudaFree(m->fbuf);
   cudaFree(m->d_face_tiles);
   cudaFree(m->d_cell_inst);
@@ -433,6 +435,7 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (dim == 2) {
     e = prepare2(pde, N);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_lq, sizeof(unsigned int));
     if (e == cudaSuccess) e = build_stage_tiles(m, tv && tv->stage_ty ? tv->stage_ty : 8);
     if (e != cudaSuccess) {
       dg_mesh_destroy(m);
@@ -485,6 +488,7 @@ static L args(dg_mesh* m, int un, int us, int out) {
   a.cap = m->ctot;
   a.bc = m->bc;
   a.gam = m->gamma;
+  a.lq = m->d_lq;
   return a;
 }
 

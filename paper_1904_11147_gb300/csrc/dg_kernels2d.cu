@@ -1176,19 +1176,31 @@ __global__ void __launch_bounds__(128)
 // quad owns conserved variable q for the subcell averages and the projection, and
 // characteristic field q in the two sweeps; the quad exchanges values with shuffles, so
 // all lanes run the same FP64 instruction stream (the FP64 pipe is the bottleneck) while
-// each thread holds a quarter of the per-cell state.
+// each thread holds a quarter of the per-cell state.  With a work counter (lq, zero at
+// launch) every warp takes its next 8 cells from it, so the work spreads evenly over the
+// resident warps whatever the grid; without one the warps stride over the list.
 template <int N>
 __global__ void __launch_bounds__(128)
     k_limit2_euler_quad(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc,
                         const int* __restrict__ list_cell, const int* __restrict__ list_inst,
-                        const Counters* __restrict__ cnt, double* __restrict__ lim, long long cap, double gam) {
+                        const Counters* __restrict__ cnt, double* __restrict__ lim, long long cap, double gam,
+                        unsigned int* __restrict__ lq) {
   using O = Off<N>;
   constexpr int NP = np_of(2, N), NS = O::NS, NG = O::NG, N1 = N + 1;
   const unsigned int n = cnt->n_flag;
   const int lane = threadIdx.x & 31, q = lane & 3, qb = lane & ~3;
   const unsigned int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned int base = warp * 8u; base < n; base += nwarps * 8u) {
+  for (unsigned int it = 0;; ++it) {
+    unsigned int base;
+    if (lq) {
+      unsigned int b0 = 0;
+      if (lane == 0) b0 = atomicAdd(lq, 8u);
+      base = __shfl_sync(0xffffffffu, b0, 0);
+    } else {
+      base = (warp + it * nwarps) * 8u;
+    }
+    if (base >= n) break;
     const unsigned int i0 = base + (lane >> 2);
     const bool active = i0 < n;
     const unsigned int i = active ? i0 : n - 1;  // idle quads repeat a valid entry
@@ -1473,9 +1485,10 @@ void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* 
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
                    double* lim, int nblocks) {
   if (pde == 1) {  // Euler: four lanes per troubled cell
-    if (N == 1) k2::k_limit2_euler_quad<1><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
-    else if (N == 2) k2::k_limit2_euler_quad<2><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
-    else k2::k_limit2_euler_quad<3><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam);
+    if (a.lq) cudaMemsetAsync(a.lq, 0, sizeof(unsigned int), a.st);
+    if (N == 1) k2::k_limit2_euler_quad<1><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
+    else if (N == 2) k2::k_limit2_euler_quad<2><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
+    else k2::k_limit2_euler_quad<3><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
     return;
   }
   DG_DISPATCH2(pde, N, (k2::k_limit2<P_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt,

@@ -17,6 +17,7 @@ struct LaunchArgs {
   long long ctot, ncell, cap;
   int bc;
   double gam;
+  unsigned int* lq;  // work counter of the 2D Euler limiter (zeroed by its launcher), or null
 };
 
 // Inference weights of the learned indicator (device pointers): W1 BF16 [32][FP] (rows
