@@ -66,11 +66,13 @@ def stage_flops_per_cell(dim: int, pde: int, N: int, faces_per_cell: float = 2.0
     face = 2 * trace + Q * llf + proj
     # cell pass, per cell
     vflux = 18 if pde == 1 else 2
-    if pde == 1 and N == 3:  # direct form: t_b per x point, products at every point
-        ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
+    if pde == 1 and N == 3:  # t_b at one x point at a time (modes in shared memory)
         tb = Q * V * sum(1 + 2 * (N - b) for b in range(N + 1))
         cols = Q * V * eval_gauss()
-        red = Q * Q * V * 2 * (sum(1 for a, b in ab if a >= 1) + sum(1 for a, b in ab if b >= 1))
+        per_x = 4 * pairs + 2 * N * (1 + 2 * (pairs - 1))
+        per_x += 2 * sum(1 for b in range(N) for a in range(1, N - b + 1))
+        per_x += 2 * sum(1 for b in range(1, N + 1) for a in range(0, N - b + 1))
+        red = Q * V * per_x
     else:
         tb = 0
         for qp in range((Q + 1) // 2):

@@ -646,11 +646,19 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
   if (ix >= I.nx || iy >= I.ny) return;
   const long long g = I.off + (long long)iy * I.nx + ix;
   const double gm1 = gam - 1.0;
+  // Euler P3 keeps the cell's modes in shared memory (one slot per thread and mode: no
+  // sharing, no barrier), which leaves the registers to the sum factorisation
+  constexpr bool kSmemU = PDE == 1 && N == 3;
+  extern __shared__ double s_u[];
   double u[V][NP];
 #pragma unroll
   for (int v = 0; v < V; ++v)
 #pragma unroll
-    for (int m = 0; m < NP; ++m) u[v][m] = __ldg(us + (long long)(v * NP + m) * ctot + g);
+    for (int m = 0; m < NP; ++m) {
+      const double x = __ldg(us + (long long)(v * NP + m) * ctot + g);
+      if constexpr (kSmemU) s_u[(v * NP + m) * 256 + threadIdx.x] = x;
+      else u[v][m] = x;
+    }
   // volume term, unscaled: X_ab = sum_q w w f psi_a' psi_b (a >= 1), Y_ab likewise with g (b >= 1),
   // sum-factorised: for every x point the column sums over y, then the x weights
   double X[V][NP], Y[V][NP];
@@ -658,7 +666,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
   for (int v = 0; v < V; ++v)
 #pragma unroll
     for (int m = 0; m < NP; ++m) X[v][m] = Y[v][m] = 0.0;
-  if constexpr (PDE == 1 && N == 3) {
+  if constexpr (kSmemU) {
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
       double tb[V][N + 1];
@@ -666,9 +674,10 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
       for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int b = 0; b <= N; ++b) {
-          double t = u[v][mode_idx(0, b)] * T(O::PQ + qx * (N + 1));
+          double t = s_u[(v * NP + mode_idx(0, b)) * 256 + threadIdx.x] * T(O::PQ + qx * (N + 1));
 #pragma unroll
-          for (int a = 1; a <= N - b; ++a) t = fma(u[v][mode_idx(a, b)], T(O::PQ + qx * (N + 1) + a), t);
+          for (int a = 1; a <= N - b; ++a)
+            t = fma(s_u[(v * NP + mode_idx(a, b)) * 256 + threadIdx.x], T(O::PQ + qx * (N + 1) + a), t);
           tb[v][b] = t;
         }
       double col[V][Q];
@@ -679,23 +688,59 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
 #pragma unroll
         for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
       }
+      // column sums over symmetric pairs of y points: G_b = sum_y w psi_b(y) f (b < N),
+      // H_b = sum_y w psi_b'(y) g (b >= 1), stored at H[b - 1]; Q = N + 1 is even here
+      static_assert((Q & 1) == 0, "P3: no middle point");
+      double G[V][N], H[V][N];
 #pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        const int q = qy * Q + qx;
-        const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
-        const double r = rcp_d(rho);
-        const double vx = mx * r, vy = my * r;
-        const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
-        const double ep = E + p;
-        const double f[V] = {mx, fma(mx, vx, p), my * vx, ep * vx};
-        const double gg[V] = {my, f[2], fma(my, vy, p), ep * vy};
+      for (int qp = 0; qp < Q / 2; ++qp) {
+        double fA[V], gA[V], fB[V], gB[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v)
+        for (int side = 0; side < 2; ++side) {
+          const int qy = side == 0 ? qp : Q - 1 - qp;
+          const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
+          const double r = rcp_d(rho);
+          const double vx = mx * r, vy = my * r;
+          const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
+          const double ep = E + p;
+          double* f = side == 0 ? fA : fB;
+          double* gg = side == 0 ? gA : gB;
+          f[0] = mx;
+          f[1] = fma(mx, vx, p);
+          f[2] = my * vx;
+          f[3] = ep * vx;
+          gg[0] = my;
+          gg[1] = f[2];
+          gg[2] = fma(my, vy, p);
+          gg[3] = ep * vy;
+        }
 #pragma unroll
-          for (int m = 1; m < NP; ++m) {
-            if (mode_a(m) >= 1) X[v][m] = fma(f[v], T(O::VDX + q * NP + m), X[v][m]);
-            if (mode_b(m) >= 1) Y[v][m] = fma(gg[v], T(O::VDY + q * NP + m), Y[v][m]);
+        for (int v = 0; v < V; ++v) {
+          const double fS = fA[v] + fB[v], fD = fA[v] - fB[v], gS = gA[v] + gB[v], gD = gA[v] - gB[v];
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            const double x = (b & 1) ? fD : fS;
+            G[v][b] = qp == 0 ? x * T(O::WPQ + b) : fma(x, T(O::WPQ + qp * (N + 1) + b), G[v][b]);
           }
+#pragma unroll
+          for (int b = 1; b <= N; ++b) {
+            const double x = (b & 1) ? gS : gD;
+            H[v][b - 1] = qp == 0 ? x * T(O::WDQ + b) : fma(x, T(O::WDQ + qp * (N + 1) + b), H[v][b - 1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+#pragma unroll
+        for (int b = 0; b < N; ++b)
+#pragma unroll
+          for (int a = 1; a <= N - b; ++a)
+            X[v][mode_idx(a, b)] = fma(T(O::WDQ + qx * (N + 1) + a), G[v][b], X[v][mode_idx(a, b)]);
+#pragma unroll
+        for (int b = 1; b <= N; ++b)
+#pragma unroll
+          for (int a = 0; a <= N - b; ++a)
+            Y[v][mode_idx(a, b)] = fma(T(O::WPQ + qx * (N + 1) + a), H[v][b - 1], Y[v][mode_idx(a, b)]);
       }
     }
   } else {
@@ -1442,6 +1487,11 @@ static cudaError_t prep_stage2() {
   cudaError_t e = cudaFuncSetAttribute(k2::k_stage2<PDE, N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)stage_smem2<PDE, N, 8>());
   if (e != cudaSuccess) return e;
+  if (PDE == 1 && N == 3) {
+    e = cudaFuncSetAttribute(k2::k_cell2<PDE, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 4 * 10 * 256));
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k2::k_stage2<PDE, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)stage_smem2<PDE, N, 4>());
 }
@@ -1458,12 +1508,17 @@ static void run_stage2(const LaunchArgs& a, int stage, double dt_all, int* queue
   k2::k_stage2<PDE, N, TYS><<<queue ? grid : a.ntiles, (TYS + 3) * 32, bytes, a.st>>>(
       a.un, a.us, a.out, a.inst, a.tiles, a.ctot, a.bc, stage, dt_all, a.gam, a.ntiles, queue);
 }
+// dynamic shared memory of the cell pass: the modes of its 256 cells for Euler P3
+static constexpr size_t cell_smem2(int pde, int N) {
+  return pde == 1 && N == 3 ? sizeof(double) * 4 * 10 * 256 : 0;
+}
+
 // split form: the face pass over the face tiles, then the cell pass over the 32 x 8 cell tiles
 void launch_stage2_split(int pde, int N, const LaunchArgs& a, int stage, double dt_all, const Tile* face_tiles,
                          int nface_tiles, double* fx, long long fxt, double* fy, long long fyt) {
   DG_DISPATCH2(pde, N, (k2::k_face2<P_, N_><<<nface_tiles, 128, 0, a.st>>>(a.us, a.inst, face_tiles, a.ctot, a.bc,
                                                                             a.gam, fx, fxt, fy, fyt)));
-  DG_DISPATCH2(pde, N, (k2::k_cell2<P_, N_><<<a.ntiles, 256, 0, a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
+  DG_DISPATCH2(pde, N, (k2::k_cell2<P_, N_><<<a.ntiles, 256, cell_smem2(P_, N_), a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
                                                                          stage, dt_all, fx, fxt, fy, fyt, a.gam)));
 }
 int tile_w2() { return k2::TX; }
