@@ -26,7 +26,9 @@ struct PpTab {
 
 // Calls f(w) with the V point values of the modes u[0..V-1] at every check point: in 1D
 // the Gauss-Lobatto points; in 2D (Gauss x Gauss-Lobatto) then (Gauss-Lobatto x Gauss),
-// by sum factorisation over the Gauss coordinate.
+// by sum factorisation over the Gauss coordinate.  Both point sets are symmetric about 0
+// and psi_n has the parity of n, so even and odd parts are summed once per pair of points
+// (psi_n(0) = 0 for odd n).  The order of the points is not part of the result (minima).
 template <int DIM, int N, int V, class F>
 __device__ __forceinline__ void for_points(const double (*u)[np_of(DIM, N)], const PpTab& tb, F&& f) {
   constexpr int L = N == 1 ? 2 : 3, NP = np_of(DIM, N);
@@ -44,37 +46,61 @@ __device__ __forceinline__ void for_points(const double (*u)[np_of(DIM, N)], con
       f(w);
     }
   } else {
+    // values of sum_c t_c psi_c(l) at the Gauss-Lobatto points l = -1, (0,) 1
+    auto lobatto = [&](const double (&t)[V][N + 1]) {
+      double wp[V], wm[V], w0[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double ev = t[v][0] * tb.pl[L - 1][0], od = t[v][1] * tb.pl[L - 1][1];
+#pragma unroll
+        for (int c = 2; c <= N; ++c) {
+          if (c & 1) od = fma(t[v][c], tb.pl[L - 1][c], od);
+          else ev = fma(t[v][c], tb.pl[L - 1][c], ev);
+        }
+        wp[v] = ev + od;
+        wm[v] = ev - od;
+        if (L == 3) {
+          double z = t[v][0] * tb.pl[1][0];
+#pragma unroll
+          for (int c = 2; c <= N; c += 2) z = fma(t[v][c], tb.pl[1][c], z);
+          w0[v] = z;
+        }
+      }
+      f(wm);
+      if (L == 3) f(w0);
+      f(wp);
+    };
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
+      // pass 0: t_b = sum_a U_ab psi_a(g_i), point (g_i, l_j) = sum_b t_b psi_b(l_j)
+      // pass 1: t_a = sum_b U_ab psi_b(g_i), point (l_j, g_i) = sum_a t_a psi_a(l_j)
+      // Gauss points in symmetric pairs; for N = 3 one at a time (fewer registers)
+      constexpr bool kPair = N < 3;
 #pragma unroll 1
-      for (int i = 0; i <= N; ++i) {
-        // pass 0: t_b = sum_a U_ab psi_a(g_i), point (g_i, l_j) = sum_b t_b psi_b(l_j)
-        // pass 1: t_a = sum_b U_ab psi_b(g_i), point (l_j, g_i) = sum_a t_a psi_a(l_j)
-        double t[V][N + 1];
+      for (int i = 0; i < (kPair ? (N + 2) / 2 : N + 1); ++i) {
+        const bool mid = !kPair || ((N % 2 == 0) && i == N / 2);  // one point (0 for N even)
+        double tp[V][N + 1], tm[V][N + 1];
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
           for (int c = 0; c <= N; ++c) {
-            double s = 0.0;
+            double ev = 0.0, od = 0.0;
 #pragma unroll
             for (int d = 0; d <= N - c; ++d) {
               const int m = pass == 0 ? mode_idx(d, c) : mode_idx(c, d);
-              s = fma(u[v][m], tb.pg[i][d], s);
+              if (d & 1) {
+                if (!kPair) ev = fma(u[v][m], tb.pg[i][d], ev);
+                else if (!mid) od = d == 1 ? u[v][m] * tb.pg[i][d] : fma(u[v][m], tb.pg[i][d], od);
+              } else {
+                ev = d == 0 ? u[v][m] * tb.pg[i][d] : fma(u[v][m], tb.pg[i][d], ev);
+              }
             }
-            t[v][c] = s;
+            const bool has_od = !mid && c < N;
+            tp[v][c] = has_od ? ev + od : ev;  // at g_i
+            tm[v][c] = has_od ? ev - od : ev;  // at g_{N-i} = -g_i
           }
-#pragma unroll
-        for (int j = 0; j < L; ++j) {
-          double w[V];
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            double s = 0.0;
-#pragma unroll
-            for (int c = 0; c <= N; ++c) s = fma(t[v][c], tb.pl[j][c], s);
-            w[v] = s;
-          }
-          f(w);
-        }
+        lobatto(tp);
+        if (!mid) lobatto(tm);
       }
     }
   }
@@ -142,14 +168,11 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
     double eps = tb.eps0;
     if (ub[0] < eps) eps = ub[0];
     if (pb < eps) eps = pb;
-    double rmin = ub[0];
-    for_points<DIM, N, 1>(u, tb, [&](const double* w) {
-      if (w[0] < rmin) rmin = w[0];
-    });
-    double th1 = 1.0;
-    if (rmin < eps) th1 = (ub[0] - eps) / (ub[0] - rmin);
-    double th2 = 1.0;
-    for_points<DIM, N, V>(u, tb, [&](const double* w) {
+    // one pass for the density minimum and, assuming theta1 = 1 (the density needs no
+    // scaling: the usual case), the pressure factor; with theta1 < 1 a second pass redoes
+    // the pressure factor on the scaled density
+    double rmin = ub[0], th1 = 1.0, th2 = 1.0;
+    auto pressure_point = [&](const double* w) {
       double q[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) q[v] = w[v];
@@ -162,7 +185,16 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
         const double t = pp_root<V>(ub, q, eps, tb.gm1);
         if (t < th2) th2 = t;
       }
+    };
+    for_points<DIM, N, V>(u, tb, [&](const double* w) {
+      if (w[0] < rmin) rmin = w[0];
+      pressure_point(w);
     });
+    if (rmin < eps) {
+      th1 = (ub[0] - eps) / (ub[0] - rmin);
+      th2 = 1.0;
+      for_points<DIM, N, V>(u, tb, pressure_point);
+    }
     if (th1 < 1.0 || th2 < 1.0) {
       ++n_changed;
 #pragma unroll
@@ -206,7 +238,7 @@ __global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__
         for (int k = 0; k < NP; ++k) u[v][k] = U[(long long)(v * NP + k) * ctot + c];
       double vmax[2] = {0.0, 0.0}, c2max = 0.0;
       for_points<DIM, N, V>(u, tb, [&](const double* w) {
-        const double r = 1.0 / w[0], vx = w[1] * r, vy = DIM == 2 ? w[2] * r : 0.0;
+        const double r = rcp_d(w[0]), vx = w[1] * r, vy = DIM == 2 ? w[2] * r : 0.0;
         const double p = tb.gm1 * (w[V - 1] - 0.5 * w[0] * (vx * vx + vy * vy));
         const double c2 = gam * p * r;
         if (c2 >= 0.0) {  // a real sound speed (false for NaN)
