@@ -42,6 +42,12 @@ struct Tile {
 };
 
 // ----------------------------------------------------------------------------- arithmetic
+// x with its sign flipped when f (mirror images of ghost cells): an exclusive or on the
+// bit pattern, which runs on the integer pipe instead of taking an FP64 instruction.
+__device__ __forceinline__ double neg_if(double x, bool f) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)((unsigned long long)f << 63));
+}
+
 // Reciprocal and square root of the 2D Euler stage fluxes, from the hardware's ~20-bit
 // approximations refined by one step of the third-order Newton-type iteration (the error
 // e of the seed enters as e^3 ~ 1e-18): within one or two ulps of the IEEE-rounded

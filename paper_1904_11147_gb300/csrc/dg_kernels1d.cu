@@ -111,7 +111,7 @@ __device__ __forceinline__ void load_cell(const double* __restrict__ U, long lon
 #pragma unroll
     for (int n = 0; n < N1; ++n) {
       const double x = __ldg(U + (long long)(v * N1 + n) * ctot + g);
-      u[v][n] = (flip && (n & 1)) ? -x : x;
+      u[v][n] = neg_if(x, flip && (n & 1));
     }
 }
 

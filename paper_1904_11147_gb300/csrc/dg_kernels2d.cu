@@ -169,7 +169,7 @@ __device__ __forceinline__ void load_cell(const double* __restrict__ U, long lon
     for (int m = 0; m < NP; ++m) {
       double x = __ldg(U + (long long)(v * NP + m) * ctot + g);
       bool flip = (fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1));
-      u[v][m] = flip ? -x : x;
+      u[v][m] = neg_if(x, flip);
     }
 }
 
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
       for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int m = 0; m < NP; ++m)
-          if (mode_b(m) & 1) u[v][m] = -u[v][m];
+          if (mode_b(m) & 1) u[v][m] = neg_if(u[v][m], true);
       trace_one<N>(u, 1, trS);
     }
   } else if (w == TYS + 2) {  // west halo (lanes < 16) east traces, east halo west traces
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
       for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int m = 0; m < NP; ++m)
-          if (east && (mode_a(m) & 1)) u[v][m] = -u[v][m];
+          u[v][m] = neg_if(u[v][m], east && (mode_a(m) & 1));
       trace_one<N>(u, 0, tA);
 #pragma unroll
       for (int q = 0; q < Q; ++q)
@@ -564,7 +564,7 @@ __device__ __forceinline__ void face_trace(const double (&u)[V][NP], int dir, bo
 #pragma unroll
       for (int n = 1; n <= N - t; ++n) {
         const double x = u[v][dir == 0 ? mode_idx(n, t) : mode_idx(t, n)];
-        s = fma((minus && (n & 1)) ? -x : x, T(O::P1 + n), s);
+        s = fma(neg_if(x, minus && (n & 1)), T(O::P1 + n), s);
       }
       e[t] = s;
     }
@@ -1276,7 +1276,7 @@ __global__ void __launch_bounds__(128)
         for (int m = 0; m < NP; ++m) {
           const double x = __ldg(U + (long long)(q * NP + m) * ctot + gj);
           const bool flip = (fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1));
-          u[m] = flip ? -x : x;
+          u[m] = neg_if(x, flip);
         }
         constexpr int k0[3] = {0, N, N + 1};
         constexpr int kn[3] = {N, 1, N};

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_kxrcf(const double* __restrict__ U, con
         for (int n = 0; n <= N; ++n) {
           const int k = DIM == 1 ? n : (f < 2 ? mode_idx(n, 0) : mode_idx(0, n));
           const double x = P[(long long)k * ctot + gn];
-          const double xn = (mirror && (n & 1)) ? -x : x;
+          const double xn = neg_if(x, mirror && (n & 1));
           a = fma(uc[k], low ? tb.pm[n] : tb.pp[n], a);
           b = fma(xn, low ? tb.pp[n] : tb.pm[n], b);
         }

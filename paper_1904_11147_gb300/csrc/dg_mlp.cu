@@ -65,7 +65,7 @@ __device__ __forceinline__ void load_modes(const double* __restrict__ U, long lo
       const double x = __ldg(U + (long long)(v * NP + m) * ctot + g);
       const int a = DIM == 1 ? m : mode_a(m), b = DIM == 1 ? 0 : mode_b(m);
       const bool flip = (fx && (a & 1)) != (fy && (b & 1));
-      u[v][m] = flip ? -x : x;
+      u[v][m] = neg_if(x, flip);
     }
 }
 
