@@ -149,17 +149,20 @@ def test_tensor_core_inference_matches_reference():
     assert np.array_equal(fl[clear], (zr[clear] > tau).astype(np.uint8))
 
 
-def test_trained_indicator_gains():
+@pytest.mark.parametrize("tol,recall", [(0.05, 0.995), (0.2, 0.95)])
+def test_trained_indicator_gains(tol, recall):
     """The network trained on harvested data from other seeds keeps the recall of the
     limiter-relevant cells while limiting fewer cells than the TVB indicator; the learned
     run (CUDA graph with the positivity fallback) stays finite and positive, and its
     density error against a run on a mesh twice as fine stays within 5 % (L1) of the
-    plain run's."""
+    plain run's.  Two label definitions: a limiter change above 5 % at 99.5 % recall, and
+    above 20 % at 95 % recall (the benchmark's)."""
     import torch
     from paper_1904_11147_gb300 import train as T
-    net, tau, info = T.train_indicator(seeds_train=(11, 12, 13, 14), seeds_val=(21,), n=64, steps=80, epochs=4)
+    net, tau, info = T.train_indicator(seeds_train=(11, 12, 13, 14), seeds_val=(21,), n=64, steps=80, epochs=4,
+                                       tol=tol, recall=recall)
     print(info)
-    assert info["val_recall"] >= 0.99
+    assert info["val_recall"] >= recall - 0.005
     assert info["val_predicted"] < info["val_tvb_flagged"]
     n = 64
     w = W.euler_2d_quadrant(n, 2, seed=31)
