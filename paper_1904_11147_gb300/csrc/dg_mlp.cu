@@ -69,42 +69,79 @@ __device__ __forceinline__ void load_modes(const double* __restrict__ U, long lo
     }
 }
 
-// Writes the F features of cell (ix, iy) to out[k * stride] (as float, or through `put`).
+// Plane offset and mirror flags of cell (ix, iy) with the boundary condition (periodic wrap;
+// outflow: the boundary cell, odd modes in the normal direction negated).
+struct CellRef {
+  long long g;
+  bool fx, fy;
+};
+__device__ __forceinline__ CellRef cell_ref(const Inst& I, int ix, int iy, int bc) {
+  bool fx = false, fy = false;
+  if (bc == 0) {
+    ix = ix < 0 ? ix + I.nx : (ix >= I.nx ? ix - I.nx : ix);
+    iy = iy < 0 ? iy + I.ny : (iy >= I.ny ? iy - I.ny : iy);
+  } else {
+    if (ix < 0) { ix = 0; fx = true; }
+    if (ix >= I.nx) { ix = I.nx - 1; fx = true; }
+    if (iy < 0) { iy = 0; fy = true; }
+    if (iy >= I.ny) { iy = I.ny - 1; fy = true; }
+  }
+  return CellRef{I.off + (long long)iy * I.nx + ix, fx, fy};
+}
+
+// The NP modes of variable v of a cell.
+template <int DIM, int NP>
+__device__ __forceinline__ void load_var(const double* __restrict__ U, long long ctot, const CellRef& c, int v,
+                                         double (&u)[NP]) {
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    const double x = __ldg(U + (long long)(v * NP + m) * ctot + c.g);
+    const int a = DIM == 1 ? m : mode_a(m), b = DIM == 1 ? 0 : mode_b(m);
+    u[m] = neg_if(x, (c.fx && (a & 1)) != (c.fy && (b & 1)));
+  }
+}
+
+// Writes the F features of cell (ix, iy) through `put`, one variable at a time (the modes
+// of one variable of the cell and its neighbours are live at once).
 template <int DIM, int PDE, int N, typename Put>
 __device__ __forceinline__ void cell_features(const double* __restrict__ U, long long ctot, const Inst& I, int ix,
                                               int iy, int bc, double c0, Put put) {
   using D = FeatDims<DIM, PDE, N>;
   constexpr int V = D::V, NP = D::NP, NB = D::NB;
-  double own[V][NP], nb[NB][V][NP];
-  load_modes<DIM, V, NP>(U, ctot, I, ix, iy, bc, own);
-  load_modes<DIM, V, NP>(U, ctot, I, ix - 1, iy, bc, nb[0]);
-  load_modes<DIM, V, NP>(U, ctot, I, ix + 1, iy, bc, nb[1]);
+  CellRef cr[NB + 1];
+  cr[0] = cell_ref(I, ix, iy, bc);
+  cr[1] = cell_ref(I, ix - 1, iy, bc);
+  cr[2] = cell_ref(I, ix + 1, iy, bc);
   if constexpr (DIM == 2) {
-    load_modes<DIM, V, NP>(U, ctot, I, ix, iy - 1, bc, nb[2]);
-    load_modes<DIM, V, NP>(U, ctot, I, ix, iy + 1, bc, nb[3]);
+    cr[3] = cell_ref(I, ix, iy - 1, bc);
+    cr[4] = cell_ref(I, ix, iy + 1, bc);
   }
   int k = 0;
-#pragma unroll
+#pragma unroll 1
   for (int v = 0; v < V; ++v) {
-    const double mj = own[v][0] * c0;
+    double own[NP], nb[NB][NP];
+    load_var<DIM, NP>(U, ctot, cr[0], v, own);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) load_var<DIM, NP>(U, ctot, cr[c + 1], v, nb[c]);
+    const double mj = own[0] * c0;
     float d[NB];
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
-      d[c] = d2f_trunc(nb[c][v][0] * c0 - mj);
+      d[c] = d2f_trunc(nb[c][0] * c0 - mj);
       s = fmaxf(s, fabsf(d[c]));
     }
 #pragma unroll
-    for (int m = 1; m < NP; ++m) s += fabsf(d2f_trunc(own[v][m]));
+    for (int m = 1; m < NP; ++m) s += fabsf(d2f_trunc(own[m]));
     const float inv = 1.0f / (s + 1e-14f);
 #pragma unroll
     for (int c = 0; c < NB; ++c) put(k++, d[c] * inv);
 #pragma unroll
-    for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(own[v][m]) * inv);
+    for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(own[m]) * inv);
 #pragma unroll
     for (int c = 0; c < NB; ++c)
 #pragma unroll
-      for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(nb[c][v][m]) * inv);
+      for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(nb[c][m]) * inv);
   }
 }
 
@@ -297,7 +334,7 @@ __global__ void __launch_bounds__(256)
 // features, runs the network on the tensor cores and appends the kept cells to list B
 // (warp ballot + one atomic per warp).  flags[] receives the final decision.
 template <int DIM, int PDE, int N>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_mlp_filter(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc, double c0,
                  MlpInfer W, const int* __restrict__ la_cell, const int* __restrict__ la_inst,
                  const Counters* __restrict__ cnt_a, unsigned char* __restrict__ flags, Counters* cnt_b,
