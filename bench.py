@@ -96,7 +96,9 @@ def stage_flops_per_cell(dim: int, pde: int, N: int, faces_per_cell: float = 2.0
                 r += 2 * sum(1 for a in range(0, N - b + 1) if not (is_mid and a % 2 == 1))
             red += V * r
     ab = [(d - b, b) for d in range(N + 1) for b in range(d + 1)]
-    combine = V * sum((3 if (a >= 1 and b >= 1) else 1) for a, b in ab if a >= 1 or b >= 1) + 4 + 2 * (N + 1) + 2
+    # 2/h and 1/h per direction (2 divisions, 2 multiplications), the lifting coefficients
+    # -psi_n(1)/h, then (2/hx) X + (2/hy) Y per mode
+    combine = V * sum((3 if (a >= 1 and b >= 1) else 1) for a, b in ab if a >= 1 or b >= 1) + 4 + 2 * (N + 1)
     lift = V * (4 * (N + 1) + 4 * NP)
     rk = V * NP * (2 + 5 + 5) / 3.0
     cell = tb + cols + Q * Q * vflux + red + combine + lift + rk
