@@ -116,6 +116,8 @@ dg_status dg_set_dt(dg_mesh* m, const double* dt);
  *   stage 3: u^{n+1} = 1/3 u^n + 2/3 (u2 + dt L(u2))
  * L is evaluated on the current state (the previous stage, limited or not).  dt > 0 applies
  * to every instance; dt <= 0 uses the per-instance values of dg_set_dt.  No limiting.
+ * FP64 arithmetic; in 2D Euler the reciprocal of the density and the sound speed's square
+ * root are the hardware's approximations refined to within 1-2 ulp of the IEEE results.
  * Errors: DG_EINVAL (stage not 1..3), DG_ESTATE (stage s without stage s-1 before it). */
 dg_status dg_rk_stage(dg_mesh* m, int stage, double dt);
 
@@ -137,7 +139,9 @@ dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flag
  * dg_flag_cells: keeps each troubled cell's average U_0 and rebuilds modes 1..N from WENO
  * point values reconstructed on the subcells of its immediate neighbours (characteristic
  * fields for Euler; dimension by dimension in 2D).  Jacobi update: every troubled cell
- * reads the unlimited neighbours.  Errors: DG_ESTATE if no flags exist for this state. */
+ * reads the unlimited neighbours.  The reciprocals in the nonlinear weights (Eq. (14)) are
+ * the hardware's approximations refined to within 1-2 ulp.  Errors: DG_ESTATE if no flags
+ * exist for this state. */
 dg_status dg_cswenolimit(dg_mesh* m);
 
 /* The parent WENO limiter (Qiu and Shu, ref. [qs1]; the limiter Sec. 4 compares CSWENO
