@@ -139,9 +139,9 @@ dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flag
  * dg_flag_cells: keeps each troubled cell's average U_0 and rebuilds modes 1..N from WENO
  * point values reconstructed on the subcells of its immediate neighbours (characteristic
  * fields for Euler; dimension by dimension in 2D).  Jacobi update: every troubled cell
- * reads the unlimited neighbours.  The reciprocals in the nonlinear weights (Eq. (14)) are
- * the hardware's approximations refined to within 1-2 ulp.  Errors: DG_ESTATE if no flags
- * exist for this state. */
+ * reads the unlimited neighbours.  In 2D the reciprocals in the nonlinear weights
+ * (Eq. (14)) are the hardware's approximations refined to within 1-2 ulp.  Errors:
+ * DG_ESTATE if no flags exist for this state. */
 dg_status dg_cswenolimit(dg_mesh* m);
 
 /* The parent WENO limiter (Qiu and Shu, ref. [qs1]; the limiter Sec. 4 compares CSWENO
