@@ -339,3 +339,40 @@ def test_call_order_errors_and_launch_count():
         g.step(1e-4)
     torch.cuda.synchronize()
     assert g.launches - before == 18  # 3 x (face and cell passes, flags, limiter, scatter, statistics)
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_OUTFLOW])
+def test_degenerate_instances_parity(bc):
+    """2D Euler P2 instances of one cell, one row, one column and a few cells next to a
+    ragged one, in one batched mesh: every stage (face and cell passes across the instance
+    boundaries), the TVB flags (ties included: a one-cell periodic instance is its own
+    neighbour) and the CSWENO limiter match the oracle run on each instance alone."""
+    sizes = [(1, 1), (1, 5), (5, 1), (2, 3), (33, 2), (40, 17)]
+    box = (0.0, 1.0, 0.0, 1.0)
+    g = dgl.Mesh(2, 1, 2, [s[0] for s in sizes], [s[1] for s in sizes], [box] * len(sizes), bc=bc)
+    rng = np.random.default_rng(4242 + bc)
+    us = [W.random_modes(2, 1, 2, nx * ny, rng) for nx, ny in sizes]
+    os_ = [oracle.Mesh(2, 1, 2, nx, ny, box=box, bc=bc) for nx, ny in sizes]
+    g.set_modes(np.concatenate(us))
+    dt = 1e-4
+    prev = list(us)
+    for s in (1, 2, 3):
+        g.rk_stage(s, dt)
+        got = g.get_modes()
+        fl, nf, nn = g.flag_cells(dgl.IND_TVB, 0.01, want=True)
+        g.cswenolimit()
+        lim = g.get_modes()
+        off, nf_o, nn_o = 0, 0, 0
+        for i, ((nx, ny), o) in enumerate(zip(sizes, os_)):
+            sl = slice(off, off + nx * ny)
+            ref = o.rk_stage(s, dt, us[i], prev[i])
+            assert _rel(got[sl], ref) < 1e-13, (s, (nx, ny), _rel(got[sl], ref))
+            fo, nfi, nni = o.flag_tvb(ref, 0.01)
+            assert np.array_equal(fl[sl], fo), (s, (nx, ny))
+            nf_o += nfi
+            nn_o += nni
+            lref = o.limit(ref, fo)
+            assert _rel(lim[sl], lref) <= 1e-11, (s, (nx, ny), _rel(lim[sl], lref))
+            prev[i] = lref
+            off += nx * ny
+        assert nf == nf_o and nn == nn_o
