@@ -1,7 +1,11 @@
 // 2D kernels (Cartesian cells, total-degree P^N, N = 1..3; Burgers V = 1, Euler V = 4).
 //
-//   k_stage2    one SSP-RK3 stage of Eq. (5): volume quadrature, traces, local
-//               Lax-Friedrichs fluxes on shared faces, lifting, stage combination
+//   k_face2     split stage, face pass: traces of the two cells, local Lax-Friedrichs
+//               flux at the face points, projection on the transverse modes (per face)
+//   k_cell2     split stage, cell pass: volume quadrature, lifting of the four faces,
+//               stage combination (per cell); the default form of one stage of Eq. (5)
+//   k_stage2    the same stage fused in one kernel per tile (halo warps, shared faces),
+//               an autotuner alternative
 //   k_flag2     TVB minmod indicator + ballot/scan compaction of troubled cells
 //   k_limit2    CSWENO limiter (Sec. 3): Burgers one thread per troubled cell, Euler
 //               four lanes per troubled cell (k_limit2_euler_quad)
