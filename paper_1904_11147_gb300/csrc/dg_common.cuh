@@ -36,7 +36,8 @@ struct Inst {
   long long fx, fy;  // first x face / y face of the instance in the 2D face planes
 };
 
-// A tile of the 2D stage / flag kernels: instance and lower-left cell of the tile.
+// A tile of the 2D stage / flag kernels: instance and lower-left cell of the tile.  The
+// face tiles of the split stage use `pad` for the face direction (0: x faces, 1: y faces).
 struct Tile {
   int inst, x0, y0, pad;
 };
