@@ -66,6 +66,11 @@ def lib():
             l.or_rk_stage.argtypes = [M, ctypes.c_int, ctypes.c_double, _D, _D, _D]
             l.or_flag_tvb.argtypes = [M, _D, ctypes.c_double, _U8, _L]
             l.or_flag_tvb.restype = ctypes.c_long
+            l.or_flag_tvb_cells.argtypes = [M, _D, ctypes.c_double, _U8, _U8, _L]
+            l.or_flag_tvb_cells.restype = ctypes.c_long
+            l.or_flag_kxrcf_cells.argtypes = [M, _D, _U8, _U8, _L, _D]
+            l.or_flag_kxrcf_cells.restype = ctypes.c_long
+            l.or_weno_points.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_double, _D]
             l.or_csweno_limit.argtypes = [M, _D, _U8, _D, ctypes.c_double]
             l.or_step.argtypes = [M, ctypes.c_double, _D, ctypes.c_double, ctypes.c_int, ctypes.c_double, _L]
             l.or_step.restype = ctypes.c_long
@@ -162,11 +167,17 @@ class Mesh:
         lib().or_rk_stage(self._ref(), stage, dt, _dp(un), _dp(us), _dp(out))
         return out
 
-    def flag_tvb(self, u, M=0.01):
+    def flag_tvb(self, u, M=0.01, near_cells=False):
+        """TVB flags: (flags, n_flagged, n_near), plus the per-cell near-threshold bytes
+        when near_cells is set."""
         u = self._chk(u)
         fl = np.zeros(self.nx * self.ny, dtype=np.uint8)
+        nc = np.zeros(self.nx * self.ny, dtype=np.uint8)
         near = ctypes.c_long(0)
-        n = lib().or_flag_tvb(self._ref(), _dp(u), M, fl.ctypes.data_as(_U8), ctypes.byref(near))
+        n = lib().or_flag_tvb_cells(self._ref(), _dp(u), M, fl.ctypes.data_as(_U8), nc.ctypes.data_as(_U8),
+                                    ctypes.byref(near))
+        if near_cells:
+            return fl, int(n), int(near.value), nc
         return fl, int(n), int(near.value)
 
     def limit(self, u, flags, eps=1e-6):
@@ -183,14 +194,19 @@ class Mesh:
         nf = lib().or_step(self._ref(), dt, _dp(u), M, int(limit), eps, ctypes.byref(near))
         return u, int(nf), int(near.value)
 
-    def flag_kxrcf(self, u):
+    def flag_kxrcf(self, u, near_cells=False):
         """KXRCF troubled-cell flags. Returns (flags, n_flagged, n_near, ratio), ratio the
-        largest indicator value over the indicator variables of each cell."""
+        largest indicator value over the indicator variables of each cell, plus the per-cell
+        near-threshold bytes when near_cells is set."""
         u = self._chk(u)
         flags = np.zeros(self.nx * self.ny, dtype=np.uint8)
+        nc = np.zeros(self.nx * self.ny, dtype=np.uint8)
         ratio = np.zeros(self.nx * self.ny)
         near = ctypes.c_long(0)
-        nf = lib().or_flag_kxrcf(self._ref(), _dp(u), flags.ctypes.data_as(_U8), ctypes.byref(near), _dp(ratio))
+        nf = lib().or_flag_kxrcf_cells(self._ref(), _dp(u), flags.ctypes.data_as(_U8), nc.ctypes.data_as(_U8),
+                                       ctypes.byref(near), _dp(ratio))
+        if near_cells:
+            return flags, int(nf), int(near.value), ratio, nc
         return flags, int(nf), int(near.value), ratio
 
     def parent_limit(self, u, flags, eps=1e-6):
@@ -269,6 +285,15 @@ def euler_eigen(dim, gamma, direction, u):
     L = np.zeros((nv, nv))
     lib().or_euler_eigen(dim, gamma, direction, _dp(u), _dp(R), _dp(L))
     return R, L
+
+
+def weno_points(N: int, avg, eps: float = 1e-6, parent: bool = False):
+    """Point values at the Step 1 points from 2N+1 stencil averages (Steps 2-5)."""
+    a = np.ascontiguousarray(avg, dtype=np.float64)
+    assert a.shape == (2 * N + 1,)
+    out = np.zeros(2 if N == 1 else 4)
+    lib().or_weno_points(N, int(parent), _dp(a), eps, _dp(out))
+    return out
 
 
 def weno_tables(N: int, parent: bool = False, points=None):

@@ -620,28 +620,26 @@ void or_rk_stage(const or_mesh* m, int stage, double dt, const double* un, const
  *   mt(a1,a2,a3) = a1 if |a1| <= M h^2, else minmod(a1,a2,a3).
  * Conserved variables; in 2D the x test uses the east/west edge midpoints and the y test
  * the north/south ones, with h the cell width in that direction.  A cell is also counted
- * "near threshold" when one of the comparisons deciding it is within about 1e-12 relative
- * (see ulp_near).
+ * "near threshold" when one of the comparisons deciding it is within 1e-12 relative
+ * (rel_near; reporting only, the flag is the exact FP64 decision).
  * ----------------------------------------------------------------------------------*/
-/* Near-threshold window (reporting only): two non-negative doubles are "near" when their
- * IEEE-754 bit patterns differ by at most 8192 units in the last place (a relative
- * difference between 0.9e-12 and 1.8e-12); a mean difference is "near zero" when it is
- * at most 2^-40 (about 0.9e-12) of the largest magnitude in the comparison. */
-static int ulp_near(double x, double y) {
-  int64_t a, b;
-  memcpy(&a, &x, sizeof a);
-  memcpy(&b, &y, sizeof b);
-  return a - b <= 8192 && a - b >= -8192;
+/* Near-threshold window: two non-negative doubles x, y are near when
+ * |x - y| <= 1e-12 max(x, y). */
+static int rel_near(double x, double y) {
+  const double mx = x > y ? x : y;
+  return fabs(x - y) <= 1e-12 * mx;
 }
 
 static int tvb_changes(double a1, double a2, double a3, double Mh2, int* near) {
   double b1 = fabs(a1);
-  if (ulp_near(b1, Mh2)) *near = 1;
+  if (rel_near(b1, Mh2)) *near = 1;
   double mt;
   if (b1 <= Mh2) return 0;
+  /* a sign test decides minmod: a mean difference within 1e-12 of the largest magnitude
+   * in the comparison counts as near zero */
   double s = fabs(a1) > fabs(a2) ? fabs(a1) : fabs(a2);
   s = s > fabs(a3) ? s : fabs(a3);
-  if (fabs(a2) <= ldexp(s, -40) || fabs(a3) <= ldexp(s, -40)) *near = 1;
+  if (fabs(a2) <= 1e-12 * s || fabs(a3) <= 1e-12 * s) *near = 1;
   if (a1 > 0 && a2 > 0 && a3 > 0) {
     mt = a1 < a2 ? a1 : a2;
     mt = mt < a3 ? mt : a3;
@@ -653,13 +651,15 @@ static int tvb_changes(double a1, double a2, double a3, double Mh2, int* near) {
   }
   if (mt != 0.0) {
     double m23 = fabs(a2) < fabs(a3) ? fabs(a2) : fabs(a3);
-    if (ulp_near(b1, m23)) *near = 1;
+    if (rel_near(b1, m23)) *near = 1;
   }
   return mt != a1;
 }
 
-/* flags[c] = 1 if troubled; returns the count; *n_near gets the near-threshold count */
-long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* flags, long* n_near) {
+/* flags[c] = 1 if troubled; returns the count; *n_near gets the near-threshold count and
+ * near_cells[c] (optional) is 1 for each near-threshold cell */
+long or_flag_tvb_cells(const or_mesh* m, const double* u, double M, unsigned char* flags, unsigned char* near_cells,
+                       long* n_near) {
   int N = m->N, nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, N);
   or_dg_tables t;
   dg_tables(N, N + 1, &t);
@@ -684,6 +684,7 @@ long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* fla
         fl |= tvb_changes(mean - um, dp, dm, Mh2, &near);
       }
       flags[c] = (unsigned char)fl;
+      if (near_cells) near_cells[c] = (unsigned char)near;
       nf += fl;
       nn += near;
     }
@@ -721,12 +722,17 @@ long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* fla
           fl |= tvb_changes(mean - uS, dpy, dmy, My, &near);
         }
         flags[(size_t)iy * m->nx + ix] = (unsigned char)fl;
+        if (near_cells) near_cells[(size_t)iy * m->nx + ix] = (unsigned char)near;
         nf += fl;
         nn += near;
       }
   }
   if (n_near) *n_near = nn;
   return nf;
+}
+
+long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* flags, long* n_near) {
+  return or_flag_tvb_cells(m, u, M, flags, NULL, n_near);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -742,15 +748,17 @@ long or_flag_tvb(const or_mesh* m, const double* u, double M, unsigned char* fla
  * |dI^-| counts inflow faces); the indicator variables are u for Burgers and the density
  * and the total energy for Euler (either one flags the cell); neighbours follow the
  * boundary condition as in the scheme.  The decision is num > den without a division,
- * and near (reporting) when the two are within 8192 ulp.
+ * and near (reporting) when the two are within 1e-12 relative (rel_near).
  * ----------------------------------------------------------------------------------*/
 static void kx_ratio(double an, double den, double* r) {
   const double q = den > 0.0 ? an / den : (an > 0.0 ? INFINITY : 0.0);
   if (q > *r) *r = q;
 }
 
-/* ratio (optional): the largest I_j over the indicator variables (0 without inflow). */
-long or_flag_kxrcf(const or_mesh* m, const double* u, unsigned char* flags, long* n_near, double* ratio) {
+/* ratio (optional): the largest I_j over the indicator variables (0 without inflow);
+ * near_cells (optional): 1 for each near-threshold cell. */
+long or_flag_kxrcf_cells(const or_mesh* m, const double* u, unsigned char* flags, unsigned char* near_cells,
+                         long* n_near, double* ratio) {
   const int N = m->N, nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, N);
   or_dg_tables t;
   dg_tables(N, N + 1, &t);
@@ -795,12 +803,13 @@ long or_flag_kxrcf(const or_mesh* m, const double* u, unsigned char* flags, long
           if (fabs(a) > nrm) nrm = fabs(a);
         }
         const double den = hp * len * nrm, an = fabs(num);
-        if (ulp_near(an, den)) near = 1;
+        if (rel_near(an, den)) near = 1;
         if (an > den) fl = 1;
         kx_ratio(an, den, &rmax);
       }
       if (ratio) ratio[c] = rmax;
       flags[c] = (unsigned char)fl;
+      if (near_cells) near_cells[c] = (unsigned char)near;
       nf += fl;
       nn += near;
     }
@@ -855,18 +864,23 @@ long or_flag_kxrcf(const or_mesh* m, const double* u, unsigned char* flags, long
               if (fabs(a) > nrm) nrm = fabs(a);
             }
           const double den = hp * len * nrm, an = fabs(num);
-          if (ulp_near(an, den)) near = 1;
+          if (rel_near(an, den)) near = 1;
           if (an > den) fl = 1;
           kx_ratio(an, den, &rmax);
         }
         if (ratio) ratio[(size_t)iy * m->nx + ix] = rmax;
         flags[(size_t)iy * m->nx + ix] = (unsigned char)fl;
+        if (near_cells) near_cells[(size_t)iy * m->nx + ix] = (unsigned char)near;
         nf += fl;
         nn += near;
       }
   }
   if (n_near) *n_near = nn;
   return nf;
+}
+
+long or_flag_kxrcf(const or_mesh* m, const double* u, unsigned char* flags, long* n_near, double* ratio) {
+  return or_flag_kxrcf_cells(m, u, flags, NULL, n_near, ratio);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -1133,6 +1147,15 @@ static void weno_limit_g(const or_mesh* m, const double* u, const unsigned char*
     }
 }
 
+/* The 1D reconstruction (Steps 2-5) alone: from the 2N+1 stencil averages avg (the
+ * subcells of Fig. 1, or the whole cells j-N..j+N when parent is set) to the point
+ * values out[NG] at the Step 1 points (in the order or_weno_export gives them). */
+void or_weno_points(int N, int parent, const double* avg, double eps, double* out) {
+  or_weno_tables t;
+  weno_tables_build_g(N, parent, 0, NULL, &t);
+  weno_1d(&t, avg, eps, out);
+}
+
 void or_csweno_limit(const or_mesh* m, const double* u, const unsigned char* flags, double* out, double eps) {
   weno_limit_g(m, u, flags, out, eps, 0);
 }
@@ -1314,12 +1337,11 @@ long or_positivity_limit(const or_mesh* m, double* u, double eps0, long* n_bad) 
  * and, when pp is set (Euler), the positivity-preserving scaling after the limiter of
  * every stage.  *n_pp (if given) receives the number of cell changes over the three
  * stages and *n_bad the cells whose mean was not admissible. */
-/* Wave-speed bound over the check points of the positivity-preserving scaling (the
- * Gauss-Lobatto points in 1D; Gauss x Gauss-Lobatto and Gauss-Lobatto x Gauss in 2D), per
- * direction: max |v_d| + max c over the points of every cell (an upper bound of the
- * largest |v_d| + c with one square root per cell).  Zhang and Shu's condition for
- * admissible means bounds the time step by the wave speeds of these point values, not of
- * the cell means.  Points without a real sound speed are skipped.  Euler only (-1). */
+/* Largest characteristic speed |v_d| + c over the check points of the positivity-
+ * preserving scaling (the Gauss-Lobatto points in 1D; Gauss x Gauss-Lobatto and
+ * Gauss-Lobatto x Gauss in 2D), per direction.  Zhang and Shu's condition for admissible
+ * means bounds the time step by the wave speeds of these point values, not of the cell
+ * means.  Points without a real sound speed are skipped.  Euler only (returns -1). */
 int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
   if (m->pde != 1) return -1;
   const int dim = m->dim, N = m->N, nv = or_nvars(dim, 1), np = or_nmodes(dim, N);
@@ -1348,7 +1370,6 @@ int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
   out[0] = out[1] = 0.0;
   for (size_t c = 0; c < (size_t)m->nx * m->ny; ++c) {
     const double* uc = u + c * nv * np;
-    double vmax[2] = {0.0, 0.0}, c2max = 0.0;
     for (int q = 0; q < npt; ++q) {
       double w[OR_MAXV];
       for (int v = 0; v < nv; ++v) {
@@ -1356,17 +1377,11 @@ int or_max_wavespeed_points(const or_mesh* m, const double* u, double* out) {
         for (int k = 0; k < np; ++k) s += uc[v * np + k] * phi[q][k];
         w[v] = s;
       }
-      const double vx = w[1] / w[0], vy = dim == 2 ? w[2] / w[0] : 0.0;
-      const double p = (m->gamma - 1.0) * (w[nv - 1] - 0.5 * w[0] * (vx * vx + vy * vy));
-      const double c2 = m->gamma * p / w[0];
-      if (!(c2 >= 0.0)) continue; /* no real sound speed (or NaN) */
-      if (c2 > c2max) c2max = c2;
-      if (fabs(vx) > vmax[0]) vmax[0] = fabs(vx);
-      if (fabs(vy) > vmax[1]) vmax[1] = fabs(vy);
+      for (int d = 0; d < dim; ++d) {
+        const double sp = max_speed(dim, 1, m->gamma, d, w);
+        if (sp > out[d]) out[d] = sp; /* a NaN speed never compares greater */
+      }
     }
-    const double cs = sqrt(c2max);
-    for (int d = 0; d < dim; ++d)
-      if (vmax[d] + cs > out[d]) out[d] = vmax[d] + cs;
   }
   return 0;
 }

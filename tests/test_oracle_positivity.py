@@ -195,10 +195,11 @@ def test_step_with_scaling_keeps_check_points_admissible():
 
 @pytest.mark.parametrize("dim,N", [(1, 1), (1, 3), (2, 2), (2, 3)])
 def test_max_wavespeed_points(dim, N):
-    """The bound max |v_d| + max c over the check points of each cell: equal to the
-    mean-based speed for piecewise-constant data, at least the largest |v_d| + c at any
-    point, and equal to an independent numpy evaluation of the bound (points without a
-    real sound speed skipped)."""
+    """The largest |v_d| + c over the check points (Zhang and Shu's time-step condition
+    uses the wave speeds of these point values): equal to the mean-based speed for
+    piecewise-constant data, and to an independent numpy evaluation of the pointwise
+    maximum (points without a real sound speed, gamma p / rho < 0, skipped) on states with
+    many non-admissible points."""
     m = _mesh(dim, N, 7)
     rng = np.random.default_rng(90 + 10 * dim + N)
     u = W.random_modes(dim, 1, N, m.nx * m.ny, rng, smooth=0.0)
@@ -206,11 +207,9 @@ def test_max_wavespeed_points(dim, N):
     u = _hostile(dim, N, m.nx * m.ny, rng)
     q = _values(u, _basis(dim, N, _points(dim, N)))
     rho, p = q[..., 0], _pressure(q)
-    ok = (rho > 0) & (p > 0)
-    c2 = np.where(ok, G * p / np.where(ok, rho, 1.0), 0.0)
-    vel = [np.where(ok, np.abs(q[..., 1 + d] / np.where(ok, rho, 1.0)), 0.0) for d in range(dim)]
-    want = [np.max(vel[d].max(axis=1) + np.sqrt(c2.max(axis=1))) for d in range(dim)]
-    pointwise = [np.max(vel[d] + np.sqrt(c2)) for d in range(dim)]
+    c2 = G * p / rho
+    ok = c2 >= 0
+    want = [np.max(np.where(ok, np.abs(q[..., 1 + d] / rho) + np.sqrt(np.where(ok, c2, 0.0)), 0.0))
+            for d in range(dim)]
     got = m.max_wavespeed_points(u)[:dim]
-    np.testing.assert_allclose(got, want, rtol=1e-13)
-    assert all(g >= pw * (1 - 1e-14) for g, pw in zip(got, pointwise))
+    np.testing.assert_allclose(got, want, rtol=1e-12)
