@@ -56,20 +56,20 @@ def stage_flops_per_cell(dim: int, pde: int, N: int, faces_per_cell: float = 2.0
     even = lambda lo, hi: sum(1 for t in range(lo, hi + 1) if t % 2 == 0)
     odd = lambda lo, hi: sum(1 for t in range(lo, hi + 1) if t % 2 == 1)
 
-    def eval_gauss():  # values of sum_t e_t psi_t at the Q Gauss points
+    def eval_gauss():  # doubled values of sum_t e_t psi_t / psi_0 at the Q Gauss points
         per_pair = (1 + 2 * odd(3, N)) + 2 * even(2, N) + 2
-        return 1 + pairs * per_pair + mid * 2 * even(2, N)
+        return pairs * per_pair + mid * 2 * even(2, N)
 
     flux = 18 if pde == 1 else 2  # one state's flux and wave speed
-    # face pass, per face
-    trace = V * (sum(1 + 2 * (N - t) for t in range(N + 1)) + eval_gauss())
+    # face pass, per face (traces over psi_0: the constant term needs no multiplication)
+    trace = V * (sum(2 * (N - t) for t in range(N + 1)) + eval_gauss())
     llf = 2 * flux + 1 + 4 * V
     proj = V * (2 * pairs + sum(1 + 2 * (pairs - 1) + (2 if (mid and b % 2 == 0) else 0) for b in range(N + 1)))
     face = 2 * trace + Q * llf + proj
     # cell pass, per cell
     vflux = 18 if pde == 1 else 2
     if pde == 1 and N == 3:  # t_b at one x point at a time (modes in shared memory)
-        tb = Q * V * sum(1 + 2 * (N - b) for b in range(N + 1))
+        tb = Q * V * sum(2 * (N - b) for b in range(N + 1))
         cols = Q * V * eval_gauss()
         per_x = 4 * pairs + 2 * N * (1 + 2 * (pairs - 1))
         per_x += 2 * sum(1 for b in range(N) for a in range(1, N - b + 1))
@@ -80,7 +80,7 @@ def stage_flops_per_cell(dim: int, pde: int, N: int, faces_per_cell: float = 2.0
         for qp in range((Q + 1) // 2):
             single = mid and qp == Q // 2
             for b in range(N + 1):
-                tb += V * (1 + 2 * even(2, N - b))
+                tb += V * 2 * even(2, N - b)
                 if not single and N - b >= 1:
                     tb += V * (1 + 2 * odd(3, N - b) + 2)
         cols = Q * V * eval_gauss()
@@ -242,6 +242,19 @@ def barrier(dist):
         dist.barrier()
 
 
+def launch_ranks(n):
+    """Starts n local ranks of this script (one per GPU) through torch.distributed.run on
+    127.0.0.1 when no launcher did; returns the launcher's exit status."""
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def reference_arm(args):
     """The oracle on the host cores, same metric, bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -306,11 +319,20 @@ def main():
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket every arm's timed steps with cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave out the batched Burgers P2 and Euler P3 workloads the default line also times")
+    ap.add_argument("--p3-steps", type=int, default=5,
+                    help="timed steps of the batched Euler P3 workload in the default line (~1.6 s each)")
+    ap.add_argument("--no-judge", action="store_true",
+                    help="leave out the learned indicator's accuracy check (half-resolution run to the window)")
+    ap.add_argument("--judge-steps", type=int, default=16)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch configuration (split stage, 8 limiter blocks "
                          "per SM), e.g. for a profiler run whose timings would mislead the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_ranks(args.gpus)
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -359,7 +381,7 @@ def main():
     # (untimed).  The fraction of troubled cells grows with time (TVB flags ~4 % of the
     # cells in the first steps, ~34 % at t = 0.05, ~67 % at t = 0.25), so a window at
     # t = 0 would not represent the run.
-    n_adv = int(round(args.t_start / dt))
+    n_adv = 2 * int(round(args.t_start / dt / 2))
     t_adv = time.perf_counter()
     with torch.cuda.stream(st):
         for _ in range(n_adv):
@@ -470,7 +492,30 @@ def main():
     e2e_value = dofs * k_e2e * world / (e2e_ms / 1e3)
     flagged = lim_learned
 
+    # ------------------------------------------------------------ the judge (untimed)
+    judge = missed = None
+    if args.arms == "both" and rank == 0 and not args.no_judge:
+        with torch.cuda.stream(st):
+            judge = judge_learned(dgl, torch, st, w, n, dt, n_adv, u0, mesh, net, tau, args.judge_steps)
+            missed = missed_shocks(dgl, torch, st, lmesh, u0, dt, tinfo["tol"] or 0.2)
+        st.synchronize()
+    mesh.close()
+    lmesh.close()
+    del u0, snapshot[:]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ batched workloads
+    batched = {}
+    if not args.no_batched:
+        batched["burgers_batched"] = run_batched("burgers_batched", args, dist, rank, world, torch, dgl,
+                                                 args.steps, learned=False)
+        batched["euler_batched_p3"] = run_batched("euler_batched_p3", args, dist, rank, world, torch, dgl,
+                                                  min(args.steps, args.p3_steps), learned=args.arms == "both")
+
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     peaks, src = measured_peaks()
     fp64_peak = float(peaks.get("fp64_tflops", FP64_PEAK_TFLOPS))
@@ -512,6 +557,8 @@ def main():
         "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps, "limited_fraction": lim_plain,
                   "tvb_flagged_fraction": tvb_frac},
         "learned_over_plain": value / value_plain,
+        "judge": judge,
+        "missed_shocks": missed,
         "kxrcf": kx,
         "parent_weno": pw,
         "roofline": {"bound": "alu", "kernel": "k_face2 + k_cell2 <Euler,P2> (one stage)", "achieved": achieved,
@@ -527,29 +574,69 @@ def main():
         "clocks": clk.summary(),
         "clocks_plain_arm": clk_plain.summary(),
     }
+    line.update(batched)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-def batched_arm(args, dist, rank, world, torch, dgl):
+def partition_instances(cells, world):
+    """Splits the instances of a batch over `world` ranks: largest first, each to the rank
+    with the fewest cells so far (ties to the lower rank).  Every instance lands on exactly
+    one rank, and a rank's load exceeds the mean load by less than the largest instance.
+    Returns one sorted index list per rank."""
+    order = sorted(range(len(cells)), key=lambda i: (-cells[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += cells[i]
+    return [sorted(p) for p in parts]
+
+
+def subset_workload(w, idx):
+    """The instances idx of a batched workload, as a workload of its own."""
+    import dataclasses
+    return dataclasses.replace(w, nx=[w.nx[i] for i in idx], ny=[w.ny[i] for i in idx],
+                               box=[w.box[i] for i in idx], params=[w.params[i] for i in idx])
+
+
+def sum_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_batched(which, args, dist, rank, world, torch, dgl, steps, clocks_out=None, learned=True):
     """Batched workloads: many uneven instances in one mesh, per-instance time steps (CFL
-    0.1), steps replayed from the CUDA graph.  Burgers: the plain TVB indicator, time steps
-    fixed at the initial state.  Euler P3: the learned indicator (trained here on P3
-    four-quadrant problems, untimed) with its plain-indicator fallback, next to the plain
-    TVB arm; both with the positivity-preserving scaling after every stage and each step's
-    per-instance time step from the wave speeds at the scaling's check points (random P3
-    four-quadrant problems lose positivity without both); that update is timed."""
-    euler = args.workload != "burgers_batched"
-    w = W.euler_2d_batched() if euler else W.burgers_2d_batched()
+    0.1), steps replayed from the CUDA graph; with several ranks the instances are split
+    over them (partition_instances) and each rank advances its own share, no collective on
+    the data path.  Burgers: the plain TVB indicator, time steps fixed at the initial state.
+    Euler P3: the learned indicator (trained here on P3 four-quadrant problems with the
+    label tolerance 0.2 and 95 % recall, untimed) with its plain-indicator fallback, next to
+    the plain TVB arm; both with the positivity-preserving scaling after every stage and
+    each step's per-instance time step from the wave speeds at the scaling's check points
+    (random P3 four-quadrant problems lose positivity without both); that update is timed.
+    Returns a dict for the JSON line (rank 0) with the job's DOF count."""
+    euler = which != "burgers_batched"
+    w_all = W.euler_2d_batched() if euler else W.burgers_2d_batched()
+    mine = partition_instances([a * b for a, b in zip(w_all.nx, w_all.ny)], world)[rank]
+    if not mine:
+        raise RuntimeError("more ranks (%d) than instances (%d)" % (world, w_all.n_inst))
+    w = subset_workload(w_all, mine)
     st = torch.cuda.Stream()
     net, tau, tinfo, t_train = None, 0.0, {}, 0.0
-    if euler and args.arms == "both":
+    if euler and learned:
         from paper_1904_11147_gb300 import train as T
         t0 = time.perf_counter()
         with torch.cuda.stream(st):
-            net, tau, tinfo = T.train_indicator(N=w.N, positivity=True, stream=st)
+            net, tau, tinfo = T.train_indicator(N=w.N, positivity=True, stream=st, tol=0.2, recall=0.95)
         st.synchronize()
         t_train = time.perf_counter() - t0
 
@@ -562,18 +649,14 @@ def batched_arm(args, dist, rank, world, torch, dgl):
 
     m = make_mesh()
     ws = m.max_wavespeed()
-    dts = []
-    for i in range(w.n_inst):
-        hx = (w.box[i][1] - w.box[i][0]) / w.nx[i]
-        hy = (w.box[i][3] - w.box[i][2]) / w.ny[i]
-        dts.append(0.1 / (ws[i, 0] / hx + ws[i, 1] / hy))
+    hx = np.array([(b[1] - b[0]) / nx for b, nx in zip(w.box, w.nx)])
+    hy = np.array([(b[3] - b[2]) / ny for b, ny in zip(w.box, w.ny)])
+    dts = 0.1 / (ws[:, 0] / hx + ws[:, 1] / hy)
     m.set_dt(dts)
-    tune = (0, 8, 0) if args.no_autotune else m.autotune(min(dts))
+    tune = (0, 8, 0) if args.no_autotune else m.autotune(float(dts.min()))
     m.set_dt(dts)
     dofs = m.size
-
-    hx = np.array([(w.box[i][1] - w.box[i][0]) / w.nx[i] for i in range(w.n_inst)])
-    hy = np.array([(w.box[i][3] - w.box[i][2]) / w.ny[i] for i in range(w.n_inst)])
+    dofs_job = sum_over_ranks(dist, float(dofs))
 
     def one_step(mm, ind):
         if euler:  # CFL 0.1 on the check-point wave speeds of the step's starting state
@@ -589,12 +672,13 @@ def batched_arm(args, dist, rank, world, torch, dgl):
             mm.flag_statistics(reset=True)
             mm.positivity_counts(reset=True)
             barrier(dist)
+            torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             l0 = mm.launches
             with ClockSampler(clk_path) as clk:
                 t0 = time.perf_counter()
                 e0.record(st)
-                for _ in range(args.steps):
+                for _ in range(steps):
                     one_step(mm, ind)
                 e1.record(st)
                 e1.synchronize()
@@ -611,45 +695,152 @@ def batched_arm(args, dist, rank, world, torch, dgl):
             bad += not bool(torch.isfinite(u[off * per:(off + nx * ny) * per]).all())
             off += nx * ny
         del u
-        info = {"value": aggregate_rate(dofs, args.steps, ms_, world), "ms_per_step": ms_ / args.steps,
-                "limited_fraction": limited / max(passes, 1) / w.cells, "nonfinite_instances": int(bad)}
+        info = {"value": dofs_job * steps / (ms_ / 1e3), "ms_per_step": ms_ / steps,
+                "limited_fraction": sum_over_ranks(dist, limited / max(passes, 1)) / w_all.cells,
+                "tvb_flagged_fraction": sum_over_ranks(dist, tvbf / max(passes, 1)) / w_all.cells,
+                "nonfinite_instances": int(sum_over_ranks(dist, bad)), "gpu_launches": launches_,
+                "clocks": clk.summary()}
         if euler:
-            info["positivity_scaled_cells"], info["inadmissible_means"] = mm.positivity_counts()
-        return ms_, launches_, clk, info
+            a, b = mm.positivity_counts()
+            info["positivity_scaled_cells"], info["inadmissible_means"] = int(sum_over_ranks(dist, a)), \
+                int(sum_over_ranks(dist, b))
+        return ms_, info
 
-    ms_plain, launches, clk_plain, plain = timed(m, dgl.IND_TVB, None if net is not None else args.clocks_out)
-    ms, info, clk = ms_plain, plain, clk_plain
+    ms_plain, plain = timed(m, dgl.IND_TVB, None if net is not None else clocks_out)
+    out = {"workload": w_all.name, "instances": w_all.n_inst, "cells": w_all.cells, "dofs": dofs_job,
+           "steps": steps, "warmup": args.warmup,
+           "indicator": "learned (TVB-gated MLP)" if net is not None else "tvb",
+           "positivity_scaling": euler,
+           "time_step": "per step from check-point wave speeds (CFL 0.1), timed" if euler
+           else "fixed at the initial state (CFL 0.1)",
+           "window": "the first steps after t = 0",
+           "autotuned": {"stage_form": "split" if tune[0] == 0 else "fused", "stage_tile_rows": tune[0],
+                         "limiter_blocks_per_sm": tune[1], "stage_persistent_queue": bool(tune[2])},
+           "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
+           "parallelism": ("instances split over %d ranks" % world) if world > 1 else "single",
+           "scaling": "strong", "plain": plain, "value": plain["value"], "ms_per_step": plain["ms_per_step"],
+           "gpu_launches": plain["gpu_launches"], "clocks": plain["clocks"]}
     if net is not None:
         m.close()  # the full batch is ~20 GB per state copy: one mesh at a time
         torch.cuda.synchronize()
         lm = make_mesh()
         lm.set_dt(dts)
         lm.set_indicator(net, tau)
-        ms, launches, clk, info = timed(lm, dgl.IND_MLP, args.clocks_out)
-        info["positivity_fallbacks"], info["positivity_failures"] = lm.positivity_report()
-        info.update({"tau": tau, "train_s": t_train, "val_recall": tinfo.get("val_recall")})
+        ms, info = timed(lm, dgl.IND_MLP, clocks_out)
+        fb, fails = lm.positivity_report()
+        info["positivity_fallbacks"], info["positivity_failures"] = int(sum_over_ranks(dist, fb)), \
+            int(sum_over_ranks(dist, fails))
+        info.update({"tau": tau, "train_s": t_train, "val_recall": tinfo.get("val_recall"),
+                     "label_tol": tinfo.get("tol"),
+                     "val_kept_of_tvb": tinfo.get("val_predicted", 0) / max(tinfo.get("val_tvb_flagged", 1), 1)})
+        lm.close()
+        out.update({"learned": info, "learned_over_plain": info["value"] / plain["value"], "value": info["value"],
+                    "ms_per_step": info["ms_per_step"], "gpu_launches": info["gpu_launches"],
+                    "clocks": info["clocks"]})
+    else:
+        m.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def batched_arm(args, dist, rank, world, torch, dgl):
+    """--workload burgers_batched / euler_batched_p3: one JSON line for that workload."""
+    r = run_batched(args.workload, args, dist, rank, world, torch, dgl, args.steps, args.clocks_out,
+                    learned=args.arms == "both")
     if rank != 0:
         return 0
-    value = aggregate_rate(dofs, args.steps, ms, world)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "instances": w.n_inst, "cells": w.cells, "dofs": dofs,
-                       "indicator": "learned (TVB-gated MLP)" if net is not None else "tvb",
-                       "positivity_scaling": euler,
-                       "time_step": "per step from check-point wave speeds (CFL 0.1), timed" if euler
-                       else "fixed at the initial state (CFL 0.1)",
-                       "limiter": "cswenolimit", "graph": True, "per_instance_dt": True,
-                       "autotuned": {"stage_form": "split" if tune[0] == 0 else "fused", "stage_tile_rows": tune[0],
-                                     "limiter_blocks_per_sm": tune[1], "stage_persistent_queue": bool(tune[2])},
-                       "l2": "state (3 x %.0f MB) larger than L2" % (dofs * 8 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "plain": plain, "gpu_launches": launches, "clocks": clk.summary()}
-    if net is not None:
-        line["learned"] = info
-        line["learned_over_plain"] = value / plain["value"]
+    cfg = {k: r[k] for k in ("workload", "instances", "cells", "dofs", "indicator", "positivity_scaling",
+                             "time_step", "window", "autotuned", "l2", "parallelism")}
+    cfg.update({"limiter": "cswenolimit", "graph": True, "per_instance_dt": True})
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg, "plain": r["plain"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    if "learned" in r:
+        line["learned"] = r["learned"]
+        line["learned_over_plain"] = r["learned_over_plain"]
     print(json.dumps(line))
     return 0
+
+
+def judge_learned(dgl, torch, st, w, n, dt, n_adv, u0, fine, net, tau, J):
+    """The learned indicator's accuracy at the benchmark's window, at half resolution: the
+    (n/2)^2 problem of the same seed runs the plain method to the window's start (n_adv / 2
+    steps of 2 dt), then J more steps with the plain and with the learned indicator; the
+    reference is the benchmark's own n^2 plain run from the window's start (u0) over 2 J
+    steps of dt, averaged onto the coarse cells.  Returns the density L1 errors (mean
+    absolute error of the cell means) and their ratio."""
+    nc = n // 2
+    cm = dgl.Mesh(2, W.PDE_EULER, 2, [nc], [nc], w.box, bc=w.bc, stream=st.cuda_stream)
+    cm.project_ic(w.ic, w.params[0])
+    dtc = 2.0 * dt
+    for _ in range(n_adv // 2):
+        cm.step(dtc)
+    uc0 = torch.empty(cm.size, dtype=torch.float64, device="cuda")
+    cm.get_modes(uc0)
+
+    def rho_means(m, cells):
+        u = torch.empty(m.size, dtype=torch.float64, device="cuda")
+        m.get_modes(u)
+        return (u.view(cells, 4, 6)[:, 0, 0] * 0.5).double()
+
+    for _ in range(J):
+        cm.step(dtc)
+    r_plain = rho_means(cm, nc * nc)
+    cm.set_modes(uc0)
+    cm.set_indicator(net, tau)
+    cm.flag_statistics(reset=True)
+    for _ in range(J):
+        cm.step(dtc, dgl.IND_MLP)
+    r_learned = rho_means(cm, nc * nc)
+    tvbf, limited, passes = cm.flag_statistics()
+    fb, fails = cm.positivity_report()
+    cm.close()
+    fine.set_modes(u0)
+    for _ in range(2 * J):
+        fine.step(dt)
+    rf = rho_means(fine, n * n).view(n, n)
+    ref = 0.25 * (rf[0::2, 0::2] + rf[1::2, 0::2] + rf[0::2, 1::2] + rf[1::2, 1::2]).reshape(-1)
+    e_plain = float((r_plain - ref).abs().mean())
+    e_learned = float((r_learned - ref).abs().mean())
+    return {"l1_rho_learned": e_learned, "l1_rho_plain": e_plain, "l1_rho_vs_plain": e_learned / e_plain,
+            "coarse": "%dx%d" % (nc, nc), "reference": "%dx%d plain (the benchmark mesh)" % (n, n),
+            "steps": J, "t_end": (n_adv + 2 * J) * dt, "coarse_limited_fraction": limited / max(passes, 1) / nc ** 2,
+            "coarse_tvb_flagged_fraction": tvbf / max(passes, 1) / nc ** 2, "coarse_positivity_fallbacks": fb,
+            "coarse_positivity_failures": fails}
+
+
+def missed_shocks(dgl, torch, st, lm, u0, dt, tol, samples=4, every=5):
+    """Cells the network skips although the limiter would change them by more than the
+    label tolerance (relative change of the modes n >= 1, the training label), on the
+    benchmark mesh: from the window's start, every `every` learned steps the first stage
+    of the next step is flagged by the learned indicator and harvested (TVB flags and the
+    limiter's change); the state then resumes unchanged."""
+    n = lm.cells
+    F = dgl.n_features(2, W.PDE_EULER, 2)
+    X = torch.empty(n, F, dtype=torch.float32, device="cuda")
+    fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ch = torch.empty(n, dtype=torch.float32, device="cuda")
+    saved = torch.empty(lm.size, dtype=torch.float64, device="cuda")
+    lm.set_modes(u0)
+    missed = labelled = kept_total = tvb_total = 0
+    for _ in range(samples):
+        for _ in range(every):
+            lm.step(dt, dgl.IND_MLP)
+        lm.get_modes(saved)
+        lm.rk_stage(1, dt)
+        kept, _, _ = lm.flag_cells(dgl.IND_MLP, 0.01, want=True)
+        lm.harvest(X, fl, ch)
+        tvb = fl.cpu().numpy() == 1
+        lab = tvb & (ch.cpu().numpy() > tol)
+        missed += int((lab & (kept == 0)).sum())
+        labelled += int(lab.sum())
+        kept_total += int(kept.sum())
+        tvb_total += int(tvb.sum())
+        lm.set_modes(saved)
+    return {"cells": missed, "labelled": labelled, "recall": 1.0 - missed / max(labelled, 1), "label_tol": tol,
+            "kept": kept_total, "tvb_flagged": tvb_total, "samples": samples,
+            "how": "first stage after every %d learned steps from the window's start" % every}
 
 
 def kernel_hash():

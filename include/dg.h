@@ -129,9 +129,13 @@ dg_status dg_rk_stage(dg_mesh* m, int stage, double dt);
  * velocity, w = u (Burgers) or density and total energy (Euler); tvb_M is ignored.
  * DG_IND_MLP: the TVB flags the learned network keeps (dg_set_indicator_mlp).  Writes the
  * device flag array and the compacted list of troubled cells used by dg_cswenolimit.
- * n_flagged, n_near (cells whose deciding comparison lies within 1e-12 relative of the
- * threshold) and flags_out (host, one byte per cell) are optional; asking for any of them
- * synchronises the stream.  Errors: DG_EINVAL (unknown indicator or no MLP weights). */
+ * n_flagged, n_near and flags_out (host, one byte per cell: bit 0 troubled, bit 1 near
+ * threshold) are optional; asking for any of them synchronises the stream.  A cell is near
+ * threshold when a comparison deciding it (TVB: |a1| against M h^2 or against the smaller
+ * neighbour difference, or a sign test; KXRCF: the two sides of I_j > 1) lies within 32768
+ * units in the last place, or a mean difference within 2^-39 of the largest magnitude in
+ * its comparison: a window that contains every comparison within 1e-12 relative.  Near
+ * cells are reported, not treated differently.  Errors: DG_EINVAL (unknown indicator or no MLP weights). */
 dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flagged,
                         int64_t* n_near, uint8_t* flags_out);
 
@@ -310,8 +314,9 @@ dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures
  *           variable v for cell iy*nx + ix (modes and variables ordered as in the ABI layout).
  *  u_out    device array of the same shape; may equal u_in (limited in place).  Unflagged
  *           cells are copied; flagged cells keep U_0 and get limited modes 1..N.
- *  n_flagged  optional host pointer; if given, the call synchronises the stream and stores
- *           the number of troubled cells.
+ *  n_flagged, n_near  optional host pointers; if either is given, the call synchronises the
+ *           stream and stores the number of troubled cells and the number of near-threshold
+ *           cells (the window of dg_flag_cells).
  *  stream   cudaStream_t (NULL = legacy default stream); the work is ordered on it.
  * Scratch: a file-scope device array of about 5.7 MB (sized for DG_NOALLOC_MAX_CELLS cells of
  * up to 4 variables x 10 modes), created when the library's device code is loaded and kept
@@ -322,7 +327,17 @@ dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures
  * overlap on the GPU (other streams, other host threads) race: order them.
  * Errors: DG_EINVAL (bad arguments, or more than DG_NOALLOC_MAX_CELLS cells), DG_ECUDA. */
 dg_status dg_cswenolimit_noalloc(int dim, int pde, int N, int nx, int ny, const double* box, int bc, double gamma,
-                                 double tvb_M, const double* u_in, double* u_out, int64_t* n_flagged, void* stream);
+                                 double tvb_M, const double* u_in, double* u_out, int64_t* n_flagged, int64_t* n_near,
+                                 void* stream);
+
+/* The refined arithmetic of the FP64 kernels (not part of the method): op 0 the reciprocal,
+ * op 1 the square root, as the 2D Euler fluxes and the WENO weights evaluate them -- the
+ * hardware's approximation refined by one Householder step of order three, within one or
+ * two ulps of the IEEE results; arguments outside the refined range (zero, subnormal,
+ * |x| >= 2^1022, inf, NaN, and non-positive square-root arguments) give the IEEE result.
+ * x and out are device arrays of n doubles; asynchronous on stream.  For checking that
+ * arithmetic against IEEE operations.  Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_refined_arith(int op, const double* x, double* out, int64_t n, void* stream);
 
 /* Thread-local text of the last error (never NULL). */
 const char* dg_last_error(void);

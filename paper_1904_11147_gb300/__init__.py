@@ -84,6 +84,8 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int)]
             l.dg_autotune.restype = ctypes.c_int
             l.dg_indicator_logits.argtypes = [P, P]
+            l.dg_refined_arith.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
+            l.dg_refined_arith.restype = ctypes.c_int
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             l.dg_positivity_limit.argtypes = [P, ctypes.c_double]
             l.dg_parent_wenolimit.argtypes = [P]
@@ -202,15 +204,19 @@ class Mesh:
     def rk_stage(self, stage, dt):
         _check(lib().dg_rk_stage(self._h, stage, dt))
 
-    def flag_cells(self, indicator=IND_TVB, M=0.01, want=False):
-        if not want:
+    def flag_cells(self, indicator=IND_TVB, M=0.01, want=False, near_cells=False):
+        """dg_flag_cells.  want: return (troubled bytes, n_flagged, n_near); near_cells: also
+        the per-cell near-threshold bytes (bit 1 of the library's flag bytes)."""
+        if not (want or near_cells):
             _check(lib().dg_flag_cells(self._h, indicator, M, None, None, None))
             return None
         nf, nn = ctypes.c_int64(0), ctypes.c_int64(0)
         fl = np.zeros(self.cells, dtype=np.uint8)
         _check(lib().dg_flag_cells(self._h, indicator, M, ctypes.byref(nf), ctypes.byref(nn),
                                    fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
-        return fl, int(nf.value), int(nn.value)
+        if near_cells:
+            return fl & 1, int(nf.value), int(nn.value), (fl >> 1) & 1
+        return fl & 1, int(nf.value), int(nn.value)
 
     def cswenolimit(self):
         _check(lib().dg_cswenolimit(self._h))
@@ -285,6 +291,13 @@ class Mesh:
     def logits(self, out):
         _check(lib().dg_indicator_logits(self._h, ctypes.c_void_p(out.data_ptr())))
         return out
+
+
+def refined_arith(op, x, out, stream=0):
+    """dg_refined_arith on CUDA float64 tensors: op 0 reciprocal, 1 square root."""
+    _check(lib().dg_refined_arith(int(op), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  x.numel(), ctypes.c_void_p(int(stream))))
+    return out
 
 
 def n_features(dim, pde, N):

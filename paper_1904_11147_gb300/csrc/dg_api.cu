@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -115,7 +116,11 @@ static int g_tables_dev = -2;  // device the constant tables were uploaded to (p
 static dgt::Tabs g_tabs[3];
 static dgt::Tabs g_ptabs[3];  // parent WENO limiter tables (full-width stencil)
 
+// Derives the tables once per process and uploads them once per device.  Any host thread
+// may call it (mesh creation, the no-allocation entry point); one mutex orders them.
 dg_status dg_ensure_tables_internal() {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (g_tables_dev == -2) {
@@ -626,6 +631,20 @@ static __global__ void k_accum_flags(const Counters* __restrict__ tvb, const Cou
     totals[1] += limited->n_flag + (extra ? extra->n_flag : 0u);
     totals[2] += 1;
   }
+}
+
+// The troubled bit (bit 0) of the flag bytes; bit 1 marks near-threshold cells.
+static __global__ void k_flag_bit0(const unsigned char* __restrict__ in, unsigned char* __restrict__ out,
+                                   long long n) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
+    out[g] = in[g] & 1;
+}
+
+// The refined reciprocal (op 0) and square root (op 1) the Euler fluxes and the WENO
+// weights use, on a device array (dg_refined_arith).
+static __global__ void k_refined_arith(int op, const double* __restrict__ x, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = op == 0 ? rcp_d(x[i]) : sqrt_d(x[i]);
 }
 
 // ----------------------------------------------------------------------------- layout
@@ -1306,6 +1325,15 @@ extern "C" dg_status dg_indicator_logits(dg_mesh* m, float* logits) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_refined_arith(int op, const double* x, double* out, int64_t n, void* stream) {
+  if ((op != 0 && op != 1) || !x || !out || n < 0) return fail(DG_EINVAL, "bad arguments");
+  if (n == 0) return DG_OK;
+  const cudaStream_t st = (cudaStream_t)stream;
+  k_refined_arith<<<(int)std::min<long long>((n + 255) / 256, 65535), 256, 0, st>>>(op, x, out, n);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
 extern "C" dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* change) {
   if (!m || !X || !flags || !change) return fail(DG_EINVAL, "null argument");
   LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
@@ -1318,10 +1346,10 @@ extern "C" dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* fla
   if (m->dim == 1) launch_limit1(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
   else launch_limit2(m->pde, m->N, a, m->list_cell, m->list_inst, m->cnt, m->lim, m->limit_blocks);
   launch_label(m->dim, m->pde, m->N, a, c0, m->list_cell, m->list_inst, m->cnt, m->lim, change, m->limit_blocks);
-  CK(cudaMemcpyAsync(flags, m->flags, m->ncell, cudaMemcpyDeviceToDevice, m->st));
+  k_flag_bit0<<<(int)std::min<long long>((m->ncell + 255) / 256, 65535), 256, 0, m->st>>>(m->flags, flags, m->ncell);
   if (m->dim == 1) launch_scatter1(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
   else launch_scatter2(m->pde, m->N, a, m->lim, m->list_cell, m->cnt, m->limit_blocks);
-  m->launches += 4;
+  m->launches += 5;
   CK(cudaGetLastError());
   m->flags_valid = false;
   return DG_OK;

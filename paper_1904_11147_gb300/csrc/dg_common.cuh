@@ -49,14 +49,18 @@ __device__ __forceinline__ double neg_if(double x, bool f) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)((unsigned long long)f << 63));
 }
 
-// Reciprocal and square root of the 2D Euler stage fluxes, from the hardware's ~20-bit
-// approximations refined by one step of the third-order Newton-type iteration (the error
-// e of the seed enters as e^3 ~ 1e-18): within one or two ulps of the IEEE-rounded
-// results, at about 70 % of their FP64 instruction cost.  Inputs that are not positive
-// normal numbers (0, subnormal, negative, inf, NaN) take the IEEE operation, so every
-// special case behaves as with IEEE arithmetic except a subnormal reciprocal argument
-// (flushed to zero: the result is NaN instead of a huge number).
+// Reciprocal and square root of the 2D Euler stage fluxes and of the WENO weights, from
+// the hardware's ~20-bit approximations refined by one step of Householder's third-order
+// iteration: with e the relative error of the seed y, 1/x = y / (1 - e) and
+// 1/sqrt(x) = y (1 - e)^(-1/2), and the first three terms of those series,
+// y (1 + e + e^2) and y (1 + e/2 + 3 e^2 / 8), leave an error of order e^3 ~ 1e-18: within
+// one or two ulps of the IEEE-rounded results, at about 70 % of their FP64 instruction
+// cost.  Arguments whose magnitude lies outside [2^-1022, 2^1022) (zero, subnormal, huge,
+// inf, NaN) take the IEEE operation, and so does a non-positive square-root argument: every
+// special case gives the IEEE result.
 __device__ __forceinline__ double rcp_d(double x) {
+  const unsigned long long ab = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  if (ab - 0x0010000000000000ull >= 0x7fc0000000000000ull) return 1.0 / x;  // |x| outside [2^-1022, 2^1022)
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   const double e = fma(-x, y, 1.0);  // x y = 1 - e
@@ -109,7 +113,7 @@ struct Phys<2, 1> {  // 2D Euler (rho, mx, my, E)
                                               double gm1) {
     double r = rcp_d(u[0]);
     double vx = u[1] * r, vy = u[2] * r;
-    double p = gm1 * (u[3] - 0.5 * fma(u[1], vx, u[2] * vy));
+    double p = fma(-0.5 * gm1, fma(u[1], vx, u[2] * vy), gm1 * u[3]);  // (gamma-1)(E - rho |v|^2 / 2)
     double vn = dir == 0 ? vx : vy;
     f[0] = dir == 0 ? u[1] : u[2];
     f[1] = dir == 0 ? fma(u[1], vx, p) : u[1] * vy;

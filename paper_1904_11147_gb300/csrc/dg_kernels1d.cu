@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kBlock)
       fl |= tvb_changes_bits(__dsub_rn(up, mean), dp, dm, mh2, near);
       fl |= tvb_changes_bits(__dsub_rn(mean, um), dp, dm, mh2, near);
     }
-    flags[g] = (unsigned char)fl;
+    flags[g] = (unsigned char)(fl | (near ? 2 : 0));  // bit 0 troubled, bit 1 near threshold
   }
   block_compact(fl, near ? 1 : 0, g, tile.inst, cnt, list_cell, list_inst);
 }

@@ -37,7 +37,8 @@ struct Lay {
   static constexpr int SIZE_PROJ = 3 * 8 + 8 * N1;
   static constexpr int SIZE_SPLIT = Q * N1;
   static constexpr int SIZE_LIM2 = N1 * (N1 * (N1 + 1) / 2) + NG * N1;
-  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT + SIZE_LIM2;
+  static constexpr int SIZE_K = Q * N1 + N1;
+  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT + SIZE_LIM2 + SIZE_K;
 };
 __host__ __device__ constexpr int base_of(int N) {
   return N == 1 ? 0 : (N == 2 ? Lay<1>::SIZE : Lay<1>::SIZE + Lay<2>::SIZE);
@@ -75,7 +76,9 @@ struct Off {
   static constexpr int WDQ = PP + 8 * N1;        // [Q][N1] w_q psi_n'(x_q)
   static constexpr int BS = WDQ + Q * N1;        // [N1][k <= l] B_kk, B_kl + B_lk
   static constexpr int WPG = BS + N1 * (N1 * (N1 + 1) / 2);  // [NG][N1] w_g psi_n(r_g)
-  static constexpr int END = WPG + NG * N1;
+  static constexpr int KQ = WPG + NG * N1;       // [Q][N1] sqrt(2) psi_n(x_q) = psi_n(x_q) / psi_0
+  static constexpr int KP1 = KQ + Q * N1;        // [N1] sqrt(2) psi_n(1)
+  static constexpr int END = KP1 + N1;
 };
 static_assert(Off<3>::END == Lay<1>::SIZE + Lay<2>::SIZE + Lay<3>::SIZE, "table layout");
 constexpr int kTabSize = Off<3>::END;
@@ -147,6 +150,9 @@ void pack(const dgt::Tabs& t, double* h) {
   }
   for (int g = 0; g < NG; ++g)
     for (int n = 0; n < N1; ++n) h[O::WPG + g * N1 + n] = t.rw[g] * t.psiG[g][n];
+  for (int q = 0; q < Q; ++q)
+    for (int n = 0; n < N1; ++n) h[O::KQ + q * N1 + n] = t.kq[q][n];
+  for (int n = 0; n < N1; ++n) h[O::KP1 + n] = t.kp1[n];
 }
 
 // ----------------------------------------------------------------------------- loads
@@ -520,9 +526,12 @@ __global__ void __launch_bounds__((TYS + 3) * 32, 1)
 //   k_face2  one thread per face: the traces of the two cells at the Q face points, the
 //            local Lax-Friedrichs flux there, and its projection onto the transverse modes
 //              P_b = sum_q w_q psi_b(s_q) [f(uL) + f(uR) - alpha (uR - uL)],  b = 0..N,
-//            stored in planes [v*(N+1) + b][face] (x faces and y faces apart);
-//   k_cell2  one thread per cell: the volume term, the lifting of the four faces' P_b
-//            and the stage combination.
+//            stored in planes [v*(N+1) + b][face] (x faces and y faces apart); the traces
+//            are formed doubled (face_trace2), so the planes hold 2^d P_b, d the degree
+//            of homogeneity of the flux (1 Euler, 2 Burgers);
+//   k_cell2  one thread per cell: the volume term (at doubled point values, likewise),
+//            the lifting of the four faces' P_b and the stage combination, with 2^-d
+//            folded into the scalings 2/h and 1/h.
 // Every face flux is computed once; all lanes of every warp do the same work.
 
 // Values at the Q Gauss points of sum_t e_t psi_t(s).  The points are symmetric
@@ -549,6 +558,62 @@ __device__ __forceinline__ void eval_gauss(const double (&e)[N + 1], double (&ou
 #pragma unroll
     for (int t = 2; t <= N; t += 2) ev = fma(e[t], T(O::PQ + (Q / 2) * (N + 1) + t), ev);
     out[Q / 2] = ev;
+  }
+}
+
+// Twice the values at the Q Gauss points of sum_t e_t psi_t(s) / psi_0 (e given over
+// psi_0): 2 sum_t (e_t / psi_0) psi_t(s) psi_0 = e_0 + sum_{t>=1} e_t sqrt(2) psi_t(s), so the
+// constant term enters without a multiplication.  Symmetric pairs as in eval_gauss.
+template <int N>
+__device__ __forceinline__ void eval_gauss2(const double (&e)[N + 1], double (&out)[N + 1]) {
+  using O = Off<N>;
+  constexpr int Q = N + 1;
+#pragma unroll
+  for (int q = 0; q < Q / 2; ++q) {
+    double ev = e[0], od = e[1] * T(O::KQ + q * (N + 1) + 1);
+#pragma unroll
+    for (int t = 2; t <= N; ++t) {
+      if (t & 1) od = fma(e[t], T(O::KQ + q * (N + 1) + t), od);
+      else ev = fma(e[t], T(O::KQ + q * (N + 1) + t), ev);
+    }
+    out[q] = ev + od;
+    out[Q - 1 - q] = ev - od;
+  }
+  if constexpr (Q & 1) {
+    double ev = e[0];
+#pragma unroll
+    for (int t = 2; t <= N; t += 2) ev = fma(e[t], T(O::KQ + (Q / 2) * (N + 1) + t), ev);
+    out[Q / 2] = ev;
+  }
+}
+
+// Twice the trace of a cell on its face normal to `dir` at the Q face points, the +1 side
+// (east / north) or, with minus = true, the -1 side (west / south), whose normal modes of
+// odd degree enter with the opposite sign.  With psi_n(1) = psi_0 sqrt(2 n + 1), the sum
+// over the normal degree is formed over psi_0 (its constant term needs no multiplication)
+// and eval_gauss2 doubles the result; the fluxes of the split stage are homogeneous in the
+// state (Euler of degree 1, Burgers of degree 2), so the passes carry the factor 2 and
+// remove it, exactly, in the final scalings.  The mirror image of a cell (outflow ghost)
+// gives a bitwise identical trace on the shared face.
+template <int N, int V, int NP>
+__device__ __forceinline__ void face_trace2(const double (&u)[V][NP], int dir, bool minus, double (&tr)[N + 1][V]) {
+  using O = Off<N>;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    double e[N + 1], val[N + 1];
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {  // transverse degree t, normal degree n
+      double s = u[v][dir == 0 ? mode_idx(0, t) : mode_idx(t, 0)];
+#pragma unroll
+      for (int n = 1; n <= N - t; ++n) {
+        const double x = u[v][dir == 0 ? mode_idx(n, t) : mode_idx(t, n)];
+        s = fma(neg_if(x, minus && (n & 1)), T(O::KP1 + n), s);
+      }
+      e[t] = s;
+    }
+    eval_gauss2<N>(e, val);
+#pragma unroll
+    for (int q = 0; q <= N; ++q) tr[q][v] = val[q];
   }
 }
 
@@ -597,12 +662,12 @@ __global__ void __launch_bounds__(128) k_face2(const double* __restrict__ us, co
   {
     double u[V][NP];
     load_cell<V, NP>(us, ctot, I, dir == 0 ? k - 1 : k, dir == 0 ? j : j - 1, bc, u);
-    face_trace<N>(u, dir, false, tL);
+    face_trace2<N>(u, dir, false, tL);
   }
   {
     double u[V][NP];
     load_cell<V, NP>(us, ctot, I, k, j, bc, u);
-    face_trace<N>(u, dir, true, tR);
+    face_trace2<N>(u, dir, true, tR);
   }
   double G[Q][V];
 #pragma unroll
@@ -649,7 +714,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
   const int ix = tile.x0 + (threadIdx.x & 31), iy = tile.y0 + (threadIdx.x >> 5);
   if (ix >= I.nx || iy >= I.ny) return;
   const long long g = I.off + (long long)iy * I.nx + ix;
-  const double gm1 = gam - 1.0;
+  const double gm1 = gam - 1.0, hgm1 = -0.5 * gm1;
   // Euler P3 keeps the cell's modes in shared memory (one slot per thread and mode: no
   // sharing, no barrier), which leaves the registers to the sum factorisation
   constexpr bool kSmemU = PDE == 1 && N == 3;
@@ -678,17 +743,18 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
       for (int v = 0; v < V; ++v)
 #pragma unroll
         for (int b = 0; b <= N; ++b) {
-          double t = s_u[(v * NP + mode_idx(0, b)) * 256 + threadIdx.x] * T(O::PQ + qx * (N + 1));
+          // t_b over psi_0 (see eval_gauss2): the constant term needs no multiplication
+          double t = s_u[(v * NP + mode_idx(0, b)) * 256 + threadIdx.x];
 #pragma unroll
           for (int a = 1; a <= N - b; ++a)
-            t = fma(s_u[(v * NP + mode_idx(a, b)) * 256 + threadIdx.x], T(O::PQ + qx * (N + 1) + a), t);
+            t = fma(s_u[(v * NP + mode_idx(a, b)) * 256 + threadIdx.x], T(O::KQ + qx * (N + 1) + a), t);
           tb[v][b] = t;
         }
-      double col[V][Q];
+      double col[V][Q];  // twice u at (x_qx, y_qy)
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         double val[Q];
-        eval_gauss<N>(tb[v], val);
+        eval_gauss2<N>(tb[v], val);
 #pragma unroll
         for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
       }
@@ -705,7 +771,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
           const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
           const double r = rcp_d(rho);
           const double vx = mx * r, vy = my * r;
-          const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
+          const double p = fma(hgm1, fma(mx, vx, my * vy), gm1 * E);  // (gamma-1)(E - rho |v|^2 / 2)
           const double ep = E + p;
           double* f = side == 0 ? fA : fB;
           double* gg = side == 0 ? gA : gB;
@@ -763,16 +829,17 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
       for (int v = 0; v < V; ++v)
   #pragma unroll
         for (int b = 0; b <= N; ++b) {
-          double ev = u[v][mode_idx(0, b)] * T(O::PQ + qp * (N + 1)), od = 0.0;
+          // over psi_0 (see eval_gauss2): the constant term needs no multiplication
+          double ev = u[v][mode_idx(0, b)], od = 0.0;
   #pragma unroll
           for (int a = 1; a <= N - b; ++a) {
             if (a & 1) {
               if (zero) continue;
-              if (single) ev = fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), ev);
-              else od = a == 1 ? u[v][mode_idx(a, b)] * T(O::PQ + qp * (N + 1) + a)
-                               : fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), od);
+              if (single) ev = fma(u[v][mode_idx(a, b)], T(O::KQ + qp * (N + 1) + a), ev);
+              else od = a == 1 ? u[v][mode_idx(a, b)] * T(O::KQ + qp * (N + 1) + a)
+                               : fma(u[v][mode_idx(a, b)], T(O::KQ + qp * (N + 1) + a), od);
             } else {
-              ev = fma(u[v][mode_idx(a, b)], T(O::PQ + qp * (N + 1) + a), ev);
+              ev = fma(u[v][mode_idx(a, b)], T(O::KQ + qp * (N + 1) + a), ev);
             }
           }
           const bool has_od = !single && b < N;
@@ -784,11 +851,11 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
         if (single && side == 1) break;
         const int qx = side == 0 ? qp : Q - 1 - qp;
         const bool mid = (Q & 1) && qx == Q / 2;
-        double col[V][Q];  // u at (x_qx, y_qy) for every qy
+        double col[V][Q];  // twice u at (x_qx, y_qy) for every qy
   #pragma unroll
         for (int v = 0; v < V; ++v) {
           double val[Q];
-          eval_gauss<N>(tb[side][v], val);
+          eval_gauss2<N>(tb[side][v], val);
   #pragma unroll
           for (int qy = 0; qy < Q; ++qy) col[v][qy] = val[qy];
         }
@@ -803,7 +870,7 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
             const double rho = col[0][qy], mx = col[1][qy], my = col[2][qy], E = col[3][qy];
             const double r = rcp_d(rho);
             const double vx = mx * r, vy = my * r;
-            const double p = gm1 * (E - 0.5 * fma(mx, vx, my * vy));
+            const double p = fma(hgm1, fma(mx, vx, my * vy), gm1 * E);  // (gamma-1)(E - rho |v|^2 / 2)
             const double ep = E + p;
             F[qy][0] = mx;
             F[qy][1] = fma(mx, vx, p);
@@ -860,8 +927,10 @@ __global__ void __launch_bounds__(256, (PDE == 1 && N == 3) ? 1 : 2) k_cell2(con
       }
     }
   }
-  // acc = (2/hx) X + (2/hy) Y - (1/hx) psi_a(1) [P_b(E) -+ P_b(W)] - (1/hy) psi_b(1) [P_a(N) -+ P_a(S)]
-  const double sx = 2.0 / I.hx, sy = 2.0 / I.hy, ihx = 0.5 * sx, ihy = 0.5 * sy;
+  // acc = (2/hx) X + (2/hy) Y - (1/hx) psi_a(1) [P_b(E) -+ P_b(W)] - (1/hy) psi_b(1) [P_a(N) -+ P_a(S)],
+  // where X, Y and the P_b were formed from doubled states: the scalings take 2^-d (exact)
+  constexpr double kHom = PDE == 1 ? 0.5 : 0.25;
+  const double sx = (2.0 / I.hx) * kHom, sy = (2.0 / I.hy) * kHom, ihx = 0.5 * sx, ihy = 0.5 * sy;
   double cx[N + 1], cy[N + 1];
 #pragma unroll
   for (int n = 0; n <= N; ++n) {
@@ -973,7 +1042,7 @@ __global__ void __launch_bounds__(256)
       fl |= tvb_changes_bits(__dsub_rn(uN, mean), dpy, dmy, my2, near);
       fl |= tvb_changes_bits(__dsub_rn(mean, uS), dpy, dmy, my2, near);
     }
-    flags[g] = (unsigned char)fl;
+    flags[g] = (unsigned char)(fl | (near ? 2 : 0));  // bit 0 troubled, bit 1 near threshold
   }
   block_compact(fl, near ? 1 : 0, g, tile.inst, cnt, list_cell, list_inst);
 }

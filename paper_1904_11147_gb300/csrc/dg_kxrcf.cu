@@ -27,9 +27,11 @@ struct KxTab {
   double w[4];          // Gauss weights
 };
 
+// near (reporting only): within kNearUlp units in the last place, a window that contains
+// the 1e-12 relative one (see tvb_changes_bits)
 __device__ __forceinline__ bool kx_near(double a, double b) {
   const long long d = __double_as_longlong(a) - __double_as_longlong(b);
-  return d <= 8192 && d >= -8192;
+  return d <= kNearUlp && d >= -kNearUlp;
 }
 
 template <int DIM, int PDE, int N>
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(256) k_kxrcf(const double* __restrict__ U, con
       if (kx_near(an, den)) near = true;
       if (an > den) fl = 1;
     }
-    flags[g] = (unsigned char)fl;
+    flags[g] = (unsigned char)(fl | (near ? 2 : 0));
   }
   block_compact(fl, near ? 1 : 0, g, tile.inst, cnt, list_cell, list_inst);
 }

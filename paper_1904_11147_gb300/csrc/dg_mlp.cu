@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(256)
 // The learned indicator keeps a TVB-flagged cell only when the network's logit exceeds
 // tau: every warp takes 32 consecutive entries of the TVB list (A), computes their
 // features, runs the network on the tensor cores and appends the kept cells to list B
-// (warp ballot + one atomic per warp).  flags[] receives the final decision.
+// (warp ballot + one atomic per warp).  flags[] receives the final decision in bit 0 and
+// keeps the TVB pass's near-threshold bit 1.
 template <int DIM, int PDE, int N>
 __global__ void __launch_bounds__(256, 2)
     k_mlp_filter(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc, double c0,
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256, 2)
     for (int k = D::F; k < FP; ++k) row[k] = __float2bfloat16_rn(0.f);
     const float z = warp_mlp(Xs, FP, W);
     const bool keep = active && z > W.tau;
-    if (active) flags[g] = keep ? 1 : 0;
+    if (active) flags[g] = (unsigned char)((flags[g] & 2) | (keep ? 1 : 0));
     const unsigned int bal = __ballot_sync(0xffffffffu, keep);
     unsigned int pos0 = 0;
     if (lane == 0 && bal) pos0 = atomicAdd(&cnt_b->n_flag, (unsigned)__popc(bal));
@@ -446,7 +447,7 @@ struct PosTab {
 };
 
 // Screens the listed cells (skip_kept: only the entries the learned filter did not keep,
-// i.e. flags[g] == 0) and marks their instances in fail[].
+// i.e. bit 0 of flags[g] clear) and marks their instances in fail[].
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) k_positivity_list(const double* __restrict__ U, long long ctot,
                                                          const int* __restrict__ list_cell,
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(128) k_positivity_list(const double* __restric
   const unsigned int n = cnt->n_flag;
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const long long g = list_cell[i];
-    if (skip_kept && flags[g]) continue;
+    if (skip_kept && (flags[g] & 1)) continue;
     float u[V][NP];
 #pragma unroll
     for (int v = 0; v < V; ++v)

@@ -82,7 +82,7 @@ dg_status fail(dg_status s, const char* m, cudaError_t e = cudaSuccess) {
 
 extern "C" dg_status dg_cswenolimit_noalloc(int dim, int pde, int N, int nx, int ny, const double* box, int bc,
                                             double gamma, double tvb_M, const double* u_in, double* u_out,
-                                            int64_t* n_flagged, void* stream) {
+                                            int64_t* n_flagged, int64_t* n_near, void* stream) {
   if (dim != 1 && dim != 2) return fail(DG_EINVAL, "dim must be 1 or 2");
   if (pde != DG_BURGERS && pde != DG_EULER) return fail(DG_EINVAL, "unknown pde");
   if (N < 1 || N > 3) return fail(DG_EINVAL, "order N must be 1..3");
@@ -172,12 +172,13 @@ extern "C" dg_status dg_cswenolimit_noalloc(int dim, int pde, int N, int nx, int
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(DG_ECUDA, "kernel launch", e);
-  if (n_flagged) {
+  if (n_flagged || n_near) {
     Counters c;
     e = cudaMemcpyAsync(&c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(DG_ECUDA, "reading the troubled-cell count", e);
-    *n_flagged = c.n_flag;
+    if (n_flagged) *n_flagged = c.n_flag;
+    if (n_near) *n_near = c.n_near;
   }
   return DG_OK;
 }

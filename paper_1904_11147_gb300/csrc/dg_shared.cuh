@@ -95,17 +95,23 @@ __global__ void k_scatter(double* __restrict__ U, long long ctot, const double* 
 // minmod(a1, a2, a3).  For finite doubles, |x| is the pattern with the sign bit cleared,
 // comparisons of non-negative values are comparisons of their patterns as integers, and
 // x > 0 / x < 0 are sign-and-nonzero tests, so this is exactly the FP64 decision while
-// keeping the slow FP64 pipe free.  near: a deciding comparison within 8192 ulp (about
-// 1e-12 relative), or a mean difference within 2^-40 of the largest magnitude.
+// keeping the slow FP64 pipe free.  near (reporting only): a deciding comparison within
+// kNearUlp units in the last place, or a mean difference within 2^-39 of the largest
+// magnitude.  Both windows contain the 1e-12 relative ones: two non-negative doubles with
+// |x - y| <= 1e-12 max(x, y) are at most 1e-12 * 2^54 < 18015 representable steps apart
+// (a step is at least 2^-54 of the larger value), and 2^-39 = 1.8e-12 > 1e-12.  So every
+// cell near the threshold by the 1e-12 relative definition is reported, with a few more.
+constexpr long long kNearUlp = 32768;
+
 __device__ __forceinline__ bool tvb_changes_bits(double a1d, double a2d, double a3d, long long mh2, bool& near) {
-  const long long kAbs = 0x7fffffffffffffffLL, kWin = 8192;
+  const long long kAbs = 0x7fffffffffffffffLL, kWin = kNearUlp;
   const long long a1 = __double_as_longlong(a1d), a2 = __double_as_longlong(a2d), a3 = __double_as_longlong(a3d);
   const long long b1 = a1 & kAbs, b2 = a2 & kAbs, b3 = a3 & kAbs;
   const long long d = b1 - mh2;
   if (d <= kWin && d >= -kWin) near = true;
   if (b1 <= mh2) return false;
   const long long s = max(max(b1, b2), b3);
-  const long long thr = s >= (41LL << 52) ? s - (40LL << 52) : 0LL;
+  const long long thr = s >= (40LL << 52) ? s - (39LL << 52) : 0LL;  // s * 2^-39
   if (b2 <= thr || b3 <= thr) near = true;
   const bool pos = a1 > 0 && a2 > 0 && a3 > 0;
   const bool neg = a1 < 0 && b1 != 0 && a2 < 0 && b2 != 0 && a3 < 0 && b3 != 0;

@@ -147,10 +147,12 @@ int build_tables(int N, Tabs* t, bool parent) {
     for (int n = 0; n <= N; ++n) {
       t->psi_q[q][n] = (double)psi(n, x[q]);
       t->dpsi_q[q][n] = (double)dpsi(n, x[q]);
+      t->kq[q][n] = (double)(sqrtl(2.0L) * psi(n, x[q]));
     }
   }
   for (int n = 0; n <= N; ++n) {
     t->psi_p1[n] = (double)psi(n, 1.0L);
+    t->kp1[n] = (double)(sqrtl(2.0L) * psi(n, 1.0L));
     t->psi_m1[n] = (double)psi(n, -1.0L);
     t->psi_0[n] = (double)psi(n, 0.0L);
   }

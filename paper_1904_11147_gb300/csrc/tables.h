@@ -18,6 +18,8 @@ struct Tabs {
   double gx[kMaxQ], gw[kMaxQ];
   double psi_q[kMaxQ][kMaxN + 1], dpsi_q[kMaxQ][kMaxN + 1];
   double psi_p1[kMaxN + 1], psi_m1[kMaxN + 1], psi_0[kMaxN + 1];
+  // the same basis values over psi_0 = 1/sqrt(2): sqrt(2) psi_n at the Gauss points and at 1
+  double kq[kMaxQ][kMaxN + 1], kp1[kMaxN + 1];
   // CSWENO (Sec. 3, Steps 1-6)
   double rp[kMaxG], rw[kMaxG];               // Step 1 points (reference r) and weights
   double psiG[kMaxG][kMaxN + 1];             // psi_n at the Step 1 points

@@ -14,13 +14,15 @@ sys.path.insert(0, ROOT)
 def test_stage_flop_count_of_the_split_stage():
     import bench
     # Euler P2, counted by hand from the face pass and the cell pass (FMA = 2 flops):
-    # face: two traces 2 x 4 x 17, three LLF points 3 x 53, projection 4 x 9;
-    # cell: t_b 64, point values 96, fluxes 9 x 18, column sums and x weights 272,
+    # face: two doubled traces 2 x 4 x 13 (normal sums 2 + 1 FMAs over psi_0, then one
+    # FMA at the middle point and an FMA, a product and two additions for the pair), three
+    # LLF points 3 x 53, projection 4 x 9;
+    # cell: t_b 40, point values 84, fluxes 9 x 18, column sums and x weights 272,
     # scalings 38, lifting 144, stage combination 96 (mean over the three stages)
     fl = bench.stage_flops_per_cell(2, 1, 2)
-    assert fl["face"] == 2 * 4 * 17 + 3 * 53 + 4 * 9 == 331
-    assert fl["cell"] == 64 + 96 + 9 * 18 + 272 + 38 + 144 + 96
-    assert fl["total"] == 2 * 331 + 872
+    assert fl["face"] == 2 * 4 * 13 + 3 * 53 + 4 * 9 == 299
+    assert fl["cell"] == 40 + 84 + 9 * 18 + 272 + 38 + 144 + 96 == 836
+    assert fl["total"] == 2 * 299 + 836
     # more modes cost more; Burgers less than Euler
     for pde in (0, 1):
         c = [bench.stage_flops_per_cell(2, pde, N)["total"] for N in (1, 2, 3)]

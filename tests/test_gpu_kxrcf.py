@@ -29,10 +29,12 @@ def test_kxrcf_flags_parity(dim, pde, N, bc):
         u = o.project_ic(W.IC_DENSITY_WAVE, [1.0, 0.2, 2 * np.pi, ky, 0.3, -0.2, 1.0])
     u[rng.uniform(size=nx * ny) < 0.05] *= 1.3
     g.set_modes(u)
-    fl, nf, nn = g.flag_cells(dgl.IND_KXRCF, 0.0, want=True)
-    fo, nfo, nno, ratio = o.flag_kxrcf(u)
-    diff = int((fl != fo).sum())
-    assert diff <= nno and abs(nn - nno) <= diff + nno, (diff, nn, nno)
+    fl, nf, nn, near = g.flag_cells(dgl.IND_KXRCF, 0.0, near_cells=True)
+    fo, nfo, nno, ratio, near_o = o.flag_kxrcf(u, near_cells=True)
+    # the two sides round differently: a flag may differ only where one of them is near
+    bad = (fl != fo) & (near == 0) & (near_o == 0)
+    assert not bad.any(), int(bad.sum())
+    assert nn == int(near.sum())
     assert 0 < nfo < nx * ny  # both kinds of cells present
     # the limiter then works on the list the indicator compacted
     g.cswenolimit()

@@ -1,10 +1,12 @@
 """GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
 
 Bars: stage outputs and projections agree to 1e-13 of the variable's scale, troubled-cell
-flags are identical (no cell lies within 1e-12 of a threshold in these inputs; the
-near-threshold counts must match too), limited modes agree to 1e-11, and after 100 full
-SSP-RK3 steps with the limiter the largest modal deviation is at most 1e-11 of the
-variable's scale (the tolerance the method's specification states for the FP64 path).
+flags are identical and the library's near-threshold cells contain the oracle's, limited
+modes agree to 1e-11 (and their modes n >= 1 to 1e-11 of their own scale), and after every
+one of 100 free-running SSP-RK3 steps with the limiter the largest modal deviation is at
+most 1e-11 of the variable's scale for P1/P2 (the tolerance the method's specification
+states for the FP64 path); for P3, where the oracle itself diverges from 1-ulp
+perturbations, at most ten times the oracle's own envelope.
 """
 import math
 
@@ -65,10 +67,11 @@ def test_flags_and_limiter_parity(dim, pde, N):
     rng = np.random.default_rng(77 + 10 * dim + 3 * pde + N)
     u = W.random_modes(dim, pde, N, nx * ny, rng, smooth=0.15 if pde == 0 else 0.02)
     g.set_modes(u)
-    fl, nf, nn = g.flag_cells(dgl.IND_TVB, 0.01, want=True)
-    fo, nfo, nno = o.flag_tvb(u, 0.01)
-    assert nf == nfo and nn == nno
-    assert np.array_equal(fl, fo)
+    fl, nf, nn, near = g.flag_cells(dgl.IND_TVB, 0.01, near_cells=True)
+    fo, nfo, nno, near_o = o.flag_tvb(u, 0.01, near_cells=True)
+    assert nf == nfo and np.array_equal(fl, fo)
+    # the library's near window contains the oracle's 1e-12 relative one
+    assert np.all(near >= near_o) and nn == int(near.sum()) and nno == int(near_o.sum())
     assert nf > 0
     g.cswenolimit()
     got = g.get_modes()
@@ -94,51 +97,10 @@ def test_projection_parity(dim, pde, N, ic, params, bc, box):
     assert _rel(g.get_modes(), ref) < 1e-13
 
 
-def _run_steps(o, g, u0, dt, steps):
-    """Advances both sides freely from u0; returns the final states, the oracle's
-    near-threshold count and the deviation after every step."""
-    import torch
-    g.set_modes(u0)
-    u = u0.copy()
-    near_total = 0
-    track = []
-    for _ in range(steps):
-        u, _, near = o.step(u, dt)
-        near_total += near
-        g.step(dt)
-        track.append(_rel(g.get_modes(), u))
-    torch.cuda.synchronize()
-    return g.get_modes(), u, near_total, track
-
-
 def _case(name, stream):
-    if name == "burgers1d_p2_k160":
-        w = W.burgers_1d(160, 2)
-        o, g = _pair(1, 0, 2, 160, box=w.box[0], bc=w.bc, stream=stream)
-        u0 = o.project_ic(w.ic, w.params[0])
-        dt = 0.1 * (2 / 160) / 1.5
-    elif name.startswith("sod"):
-        N = int(name.split("_p")[1][0])
-        w = W.shock_tube("sod", 200, N)
-        o, g = _pair(1, 1, N, 200, box=w.box[0], bc=w.bc, stream=stream)
-        u0 = o.project_ic(w.ic, w.params[0])
-        dt = 0.1 * (1 / 200) / o.max_wavespeed(u0)[0]
-    elif name.startswith("euler2d_quadrant"):
-        N = 2 if "p2" in name else 3
-        n = 40 if N == 2 else 24
-        # without a positivity limiter some random P3 quadrant states lose positivity on
-        # coarse meshes; seed 1907 stays positive for 100 steps
-        w = W.euler_2d_quadrant(n, N) if N == 2 else W.euler_2d_quadrant(n, N, seed=1907)
-        o, g = _pair(2, 1, N, n, n, box=w.box[0], bc=w.bc, stream=stream)
-        u0 = o.project_ic(w.ic, w.params[0])
-        ws = o.max_wavespeed(u0)
-        dt = 0.1 / (ws[0] * n + ws[1] * n)
-    else:
-        w = W.burgers_2d_batched(1, 2, 32, 32)
-        o, g = _pair(2, 0, 2, 32, 32, box=w.box[0], bc=w.bc, stream=stream)
-        u0 = o.project_ic(w.ic, w.params[0])
-        h = 4.0 / 32
-        dt = 0.1 / (2 * 1.6 / h)
+    from parity_cases import oracle_case
+    o, u0, dt = oracle_case(name)
+    g = dgl.Mesh(o.dim, o.pde, o.N, [o.nx], [o.ny], [o.box], bc=o.bc, stream=stream)
     return o, g, u0, dt
 
 
@@ -162,27 +124,44 @@ def test_hundred_steps_shadow_parity(name):
     assert nf > 0
 
 
+# Free-running P3 bar: the GPU's deviation from the oracle after step k is at most
+# P3_C times the oracle's own 1-ulp sensitivity envelope over steps <= k + P3_LEAD (the
+# envelope grows in jumps when a TVB decision flips, and the GPU's first flip may come a
+# few steps before the envelope's), and never above P3_FLOOR where the envelope is smaller.
+P3_C, P3_LEAD, P3_FLOOR = 10.0, 10, 1e-13
+
+
 @pytest.mark.parametrize("name", ALL_CASES)
 def test_hundred_steps_parity(name):
-    """Free-running: both sides advance 100 steps on their own.  P1/P2 stay within 1e-11
-    of each other.  With P3 the split of negative linear weights and smoothness-indicator
-    forms with entries in the thousands amplify rounding differences by about an order of
-    magnitude every 10-20 steps (a property of the scheme: the first step agrees to 1e-14),
-    so there the growth-free start is asserted (first 5 steps within 1e-12) and the full
-    track reported; the per-step agreement is asserted by the shadow test above."""
+    """Free-running: both sides advance 100 steps on their own.  P1/P2: within 1e-11 after
+    every step.  P3: the oracle run against itself from 1-ulp perturbations diverges by
+    orders of magnitude (tests/test_oracle_dg.py), so the GPU is held to that envelope:
+    after every step its deviation is at most P3_C times the envelope (see above)."""
     import torch
+    from parity_cases import oracle_case, reference_run, self_deviation
     st = torch.cuda.Stream()
-    o, g, u0, dt = _case(name, st.cuda_stream)
+    o, u0, dt = oracle_case(name)
+    g = dgl.Mesh(o.dim, o.pde, o.N, [o.nx], [o.ny], [o.box], bc=o.bc, stream=st.cuda_stream)
+    ref = reference_run(o, u0, dt, 100)
+    track = []
     with torch.cuda.stream(st):
-        got, ref, near, track = _run_steps(o, g, u0, dt, 100)
-    assert np.isfinite(ref).all()
-    err = _rel(got, ref)
-    print(name, "free-running deviation after 100 steps: %.3e, near-threshold: %d, track %s" %
-          (err, near, ["%.1e" % e for e in track[::10]]))
+        g.set_modes(u0)
+        for k in range(100):
+            g.step(dt)
+            track.append(_rel(g.get_modes(), ref[k]))
+    torch.cuda.synchronize()
+    assert np.isfinite(ref[-1]).all()
     if "_p3" in name:
-        assert max(track[:5]) <= 1e-12, track[:5]
+        env, _ = self_deviation(o, u0, dt, ref)
+        print(name, "GPU track   ", ["%.1e" % e for e in track[::10]], "%.1e" % track[-1])
+        print(name, "oracle 1-ulp", ["%.1e" % e for e in env[::10]], "%.1e" % env[-1])
+        for k in range(100):
+            bound = max(P3_FLOOR, P3_C * float(env[: min(k + P3_LEAD, 99) + 1].max()))
+            assert track[k] <= bound, (k, track[k], bound)
     else:
-        assert err <= 1e-11, (err, near, ["%.1e" % e for e in track[::10]])
+        print(name, "free-running deviation after 100 steps: %.3e, track %s" %
+              (track[-1], ["%.1e" % e for e in track[::10]]))
+        assert max(track) <= 1e-11, ["%.1e" % e for e in track[::10]]
 
 
 def test_batched_instances_parity():
@@ -359,7 +338,7 @@ def test_degenerate_instances_parity(bc):
     for s in (1, 2, 3):
         g.rk_stage(s, dt)
         got = g.get_modes()
-        fl, nf, nn = g.flag_cells(dgl.IND_TVB, 0.01, want=True)
+        fl, nf, nn, near = g.flag_cells(dgl.IND_TVB, 0.01, near_cells=True)
         g.cswenolimit()
         lim = g.get_modes()
         off, nf_o, nn_o = 0, 0, 0
@@ -367,12 +346,64 @@ def test_degenerate_instances_parity(bc):
             sl = slice(off, off + nx * ny)
             ref = o.rk_stage(s, dt, us[i], prev[i])
             assert _rel(got[sl], ref) < 1e-13, (s, (nx, ny), _rel(got[sl], ref))
-            fo, nfi, nni = o.flag_tvb(ref, 0.01)
+            fo, nfi, nni, near_o = o.flag_tvb(ref, 0.01, near_cells=True)
             assert np.array_equal(fl[sl], fo), (s, (nx, ny))
+            assert np.all(near[sl] >= near_o), (s, (nx, ny))
             nf_o += nfi
             nn_o += nni
             lref = o.limit(ref, fo)
             assert _rel(lim[sl], lref) <= 1e-11, (s, (nx, ny), _rel(lim[sl], lref))
             prev[i] = lref
             off += nx * ny
-        assert nf == nf_o and nn == nn_o
+        assert nf == nf_o and nn == int(near.sum()) >= nn_o
+
+
+def _near_data(dim, N, n, rng, Mh2):
+    """Burgers modes with many TVB comparisons within a few 1e-12 of their threshold:
+    |a1| = M h^2 (1 + d), d ~ U[-4e-12, 4e-12] in half of the cells, and neighbour mean
+    differences that equal |a1| or vanish to within 1e-12 in others (small means keep the
+    face-value cancellation far below the window)."""
+    ab = oracle.mode_ab(2, N) if dim == 2 else [(k, 0) for k in range(N + 1)]
+    ncell = n * (n if dim == 2 else 1)
+    u = np.zeros((ncell, 1, len(ab)))
+    a1 = Mh2 * (1 + rng.uniform(-4e-12, 4e-12, ncell)) * rng.choice([-1.0, 1.0], ncell)
+    far = rng.uniform(size=ncell) < 0.3
+    a1[far] *= rng.uniform(0.2, 5.0, far.sum())
+    steps = Mh2 * rng.uniform(0.5, 8.0, ncell) * rng.choice([-1.0, 1.0], ncell)
+    pick = rng.uniform(size=ncell)
+    steps[pick < 0.15] = np.abs(a1[pick < 0.15]) * (1 + rng.uniform(-4e-12, 4e-12, (pick < 0.15).sum())) * \
+        np.sign(a1[pick < 0.15])
+    tiny = (pick >= 0.15) & (pick < 0.25)
+    steps[tiny] = Mh2 * rng.uniform(-4e-12, 4e-12, tiny.sum())
+    if dim == 1:
+        mean = np.cumsum(steps)
+        u[:, 0, 0] = mean * math.sqrt(2.0)
+        u[:, 0, 1] = a1 / math.sqrt(1.5)
+    else:
+        mean = np.cumsum(steps.reshape(n, n), axis=1) + np.cumsum(steps.reshape(n, n)[:, :1] * 0.7, axis=0)
+        u[:, 0, 0] = mean.reshape(-1) * 2.0
+        k10, k01 = ab.index((1, 0)), ab.index((0, 1))
+        # u(east) - mean = U10 psi_1(1) psi_0 ;  u(north) - mean = U01 psi_0 psi_1(1)
+        u[:, 0, k10] = a1 / (math.sqrt(1.5) / math.sqrt(2.0))
+        u[:, 0, k01] = np.roll(a1, 7) / (math.sqrt(1.5) / math.sqrt(2.0))
+    return u
+
+
+@pytest.mark.parametrize("dim,N", [(1, 1), (1, 2), (1, 3), (2, 1), (2, 2), (2, 3)])
+def test_tvb_near_threshold_cells_contain_the_oracles(dim, N):
+    """Inputs built so that thousands of TVB comparisons lie within a few 1e-12 of their
+    threshold: the flags are identical to the oracle's, and every cell the oracle reports
+    near the threshold (1e-12 relative) is reported by the library too."""
+    n = 4096 if dim == 1 else 64
+    M = 0.01
+    h = 1.0 / n
+    o, g = _pair(dim, 0, N, n, n if dim == 2 else 1, box=(0.0, 1.0, 0.0, 1.0), bc=W.BC_PERIODIC)
+    u = _near_data(dim, N, n, np.random.default_rng(42 + 10 * dim + N), M * h * h)
+    g.set_modes(u)
+    fl, nf, nn, near = g.flag_cells(dgl.IND_TVB, M, near_cells=True)
+    fo, nfo, nno, near_o = o.flag_tvb(u, M, near_cells=True)
+    assert np.array_equal(fl, fo) and nf == nfo
+    assert nno > 0.05 * fl.size, nno
+    assert np.all(near >= near_o), int((near_o > near).sum())
+    assert nn == int(near.sum())
+    print("near-threshold cells: oracle %d, library %d of %d" % (nno, nn, fl.size))
