@@ -272,9 +272,11 @@ dg_status dg_mlp_predict(dg_mlp* n, const float* X, int64_t B, float* logits);
 
 /* Attach the network's current weights to the mesh as DG_IND_MLP with threshold tau.
  * DG_IND_MLP flags a cell when the TVB indicator flags it and the network's logit exceeds
- * tau (the network filters the TVB list).  In dg_step, Euler instances whose limited stage
- * has a non-positive density or pressure at a quadrature point (FP32 screen with a 1e-6 E
- * margin) are limited again with the plain TVB flags from their unlimited state. */
+ * tau (the network filters the TVB list).  In dg_step (Euler), the plain TVB indicator is
+ * the fallback, cell by cell: a TVB-flagged cell the network skipped whose unlimited stage
+ * has a non-positive density or pressure at a volume or face Gauss point (FP32 screen,
+ * p > 1e-6 |E| required) is limited as the plain method limits it, before the limiter
+ * runs; the skipped cells left unlimited therefore pass the screen. */
 dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau);
 
 /* Evaluates the network on every cell of the current state and writes the logits to the
@@ -295,7 +297,10 @@ dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* 
 dg_status dg_flag_statistics(dg_mesh* m, int64_t* tvb_flagged, int64_t* limited, int64_t* passes, int reset);
 
 /* Positivity fallbacks of the learned indicator since the network was attached: instance
- * stages that fell back to the TVB flags, and those still non-positive after it.  Returns
+ * stages in which the screen handed skipped cells back to the TVB flags, and instance
+ * stages in which a limited cell still fails the screen (as it would in the plain
+ * method; counted only while the positivity-preserving scaling is off, since with it on
+ * the scaling that follows the limiter restores the check points).  Returns
  * DG_EPOSITIVITY when failures > 0.  Synchronises the stream. */
 dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures);
 

@@ -29,8 +29,9 @@ _lock = threading.Lock()
 _lib = None
 
 PDE_BURGERS, PDE_EULER = 0, 1
-BC_PERIODIC, BC_OUTFLOW = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_DMR = 0, 1, 2
 IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+IC_DMR = 6
 
 
 def build(force: bool = False) -> str:
@@ -47,7 +48,8 @@ class _Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("pde", ctypes.c_int), ("N", ctypes.c_int),
                 ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int),
                 ("xL", ctypes.c_double), ("xR", ctypes.c_double),
-                ("yL", ctypes.c_double), ("yR", ctypes.c_double), ("gamma", ctypes.c_double)]
+                ("yL", ctypes.c_double), ("yR", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("t", ctypes.c_double), ("bcp", ctypes.c_double * 11)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -128,13 +130,20 @@ def mode_ab(dim: int, N: int):
 class Mesh:
     """One mesh instance: dim 1 or 2, pde, degree N, nx x ny cells on the box, bc."""
 
-    def __init__(self, dim, pde, N, nx, ny=1, box=(0.0, 1.0, 0.0, 1.0), bc=BC_PERIODIC, gamma=1.4):
+    def __init__(self, dim, pde, N, nx, ny=1, box=(0.0, 1.0, 0.0, 1.0), bc=BC_PERIODIC, gamma=1.4, bcp=None):
+        """bc = BC_DMR (2D Euler): bcp holds the double Mach reflection data -- post-shock
+        (rho, u, v, p), pre-shock (rho, u, v, p), and a, b, c of the shock line
+        x_s(y, t) = a + b y + c t; the attribute t is the time of the states passed."""
         if dim == 1:
             ny = 1
         self.dim, self.pde, self.N, self.nx, self.ny, self.bc = dim, pde, N, nx, ny, bc
         self.box = tuple(float(b) for b in box)
+        assert len(self.box) == 4
         self.gamma = float(gamma)
-        self._m = _Mesh(dim, pde, N, nx, ny, bc, *self.box, self.gamma)
+        self.bcp = [0.0] * 11 if bcp is None else [float(x) for x in bcp]
+        assert len(self.bcp) == 11
+        self.t = 0.0
+        self._m = _Mesh(dim, pde, N, nx, ny, bc, *self.box, self.gamma, 0.0, (ctypes.c_double * 11)(*self.bcp))
         self.nv = nvars(dim, pde)
         self.np = nmodes(dim, N)
         self.shape = (nx * ny, self.nv, self.np)
@@ -145,6 +154,7 @@ class Mesh:
         return ((xR - xL) / self.nx, (yR - yL) / self.ny if self.dim == 2 else None)
 
     def _ref(self):
+        self._m.t = float(self.t)
         return ctypes.byref(self._m)
 
     def zeros(self):

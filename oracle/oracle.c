@@ -42,9 +42,14 @@ typedef struct {
   int pde;   /* 0 Burgers, 1 Euler */
   int N;     /* polynomial degree 1..3 */
   int nx, ny;/* ny = 1 in 1D */
-  int bc;    /* 0 periodic, 1 outflow */
+  int bc;    /* 0 periodic, 1 outflow, 2 double Mach reflection (2D Euler) */
   double xL, xR, yL, yR;
   double gamma;
+  /* bc 2: the time of the state the operators are applied to, and the problem's data:
+   * post-shock (rho, u, v, p), pre-shock (rho, u, v, p), and the shock line
+   * x_s(y, t) = a + b y + c t (a is also where the wall starts on the bottom side) */
+  double t;
+  double bcp[11];
 } or_mesh;
 
 int or_nmodes(int dim, int N) { return dim == 1 ? N + 1 : (N + 1) * (N + 2) / 2; }
@@ -426,9 +431,72 @@ static void llf(int dim, int pde, double gam, int dir, const double* uL, const d
  * further ghosts (the parent WENO stencil reaches N cells out) mirror the interior cell
  * at the reflected position (ghost -1-k <-> cell k).
  * ----------------------------------------------------------------------------------*/
+/* Conserved variables of a primitive state (rho, u, v, p), 2D Euler. */
+static void prim_to_cons(double gam, const double* w, double* c) {
+  c[0] = w[0];
+  c[1] = w[0] * w[1];
+  c[2] = w[0] * w[2];
+  c[3] = w[3] / (gam - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2]);
+}
+
+/* Modes of a cell holding the constant conserved state c (2D: only U_00 = 2 c). */
+static void const_modes(int nv, int np, const double* c, double* out) {
+  for (int v = 0; v < nv; ++v)
+    for (int k = 0; k < np; ++k) out[v * np + k] = k == 0 ? 2.0 * c[v] : 0.0;
+}
+
+/* Ghost cells of the double Mach reflection problem (Example 11, after Woodward and
+ * Colella, ref. [wc]), decided by the ghost cell's centre (x_c, y_c) at the time m->t of
+ * the state:
+ *   left (x < xL): the post-shock state (inflow);
+ *   right (x > xR): the mirror image of the boundary cell (outflow);
+ *   bottom (y < yL): the post-shock state where x_c < a, else a reflecting wall: the
+ *     mirror image in y with the normal momentum rho v negated;
+ *   top (y > yR): the post-shock state where x_c < x_s(yR, t) = a + b yR + c t (the
+ *     exact position of the moving shock on that side), else the pre-shock state.
+ * The x side decides first (a corner ghost takes the left or right rule, then the bottom
+ * or top rule applies to what the right rule returned).  Ghosts further out (k > 0)
+ * mirror interior cell k. */
+static void dmr_modes(const or_mesh* m, const double* u, int ix, int iy, double* out) {
+  const int nv = 4, np = or_nmodes(2, m->N);
+  const double hx = (m->xR - m->xL) / m->nx, hy = (m->yR - m->yL) / m->ny;
+  const double xc = m->xL + (ix + 0.5) * hx;
+  const double* b = m->bcp;
+  double post[4], pre[4];
+  prim_to_cons(m->gamma, b, post);
+  prim_to_cons(m->gamma, b + 4, pre);
+  if (ix < 0) { const_modes(nv, np, post, out); return; }
+  if (iy >= m->ny) {
+    const double xs = b[8] + b[9] * m->yR + b[10] * m->t;
+    const_modes(nv, np, xc < xs ? post : pre, out);
+    return;
+  }
+  if (iy < 0 && xc < b[8]) { const_modes(nv, np, post, out); return; }
+  int fx = 0, fy = 0;
+  if (ix >= m->nx) { ix = 2 * m->nx - 1 - ix; fx = 1; }
+  if (iy < 0) { iy = -1 - iy; fy = 1; }
+  if (ix < 0) ix = 0;
+  if (iy >= m->ny) iy = m->ny - 1;
+  const double* src = u + ((size_t)iy * m->nx + ix) * nv * np;
+  for (int v = 0; v < nv; ++v)
+    for (int k = 0; k < np; ++k) {
+      int a, bb;
+      mode_ab(k, &a, &bb);
+      double s = 1.0;
+      if (fx && (a & 1)) s = -s;
+      if (fy && (bb & 1)) s = -s;
+      if (fy && v == 2) s = -s; /* reflecting wall: rho v changes sign */
+      out[v * np + k] = s * src[v * np + k];
+    }
+}
+
 static void cell_modes(const or_mesh* m, const double* u, int ix, int iy, double* out) {
   int nv = or_nvars(m->dim, m->pde), np = or_nmodes(m->dim, m->N);
   int fx = 0, fy = 0;
+  if (m->bc == 2 && (ix < 0 || ix >= m->nx || iy < 0 || iy >= m->ny)) {
+    dmr_modes(m, u, ix, iy, out);
+    return;
+  }
   if (m->bc == 0) {
     ix = (ix % m->nx + m->nx) % m->nx;
     iy = (iy % m->ny + m->ny) % m->ny;
@@ -1184,12 +1252,19 @@ long or_step(const or_mesh* m, double dt, double* u, double M, int limit, double
   long nf = 0, nn = 0, near = 0;
   memcpy(un, u, n * sizeof(double));
   const double* prev = un;
+  /* m->t is the time of u^n; stage s evaluates L at the time of u^(s-1) (t, t + dt,
+   * t + dt/2) and its output holds at t + dt, t + dt/2, t + dt (time-dependent boundary
+   * data only) */
+  const double c_in[3] = {0.0, 1.0, 0.5}, c_out[3] = {1.0, 0.5, 1.0};
+  or_mesh ms = *m;
   for (int s = 1; s <= 3; ++s) {
-    or_rk_stage(m, s, dt, un, prev, a);
+    ms.t = m->t + c_in[s - 1] * dt;
+    or_rk_stage(&ms, s, dt, un, prev, a);
+    ms.t = m->t + c_out[s - 1] * dt;
     if (limit) {
-      nf += or_flag_tvb(m, a, M, fl, &near);
+      nf += or_flag_tvb(&ms, a, M, fl, &near);
       nn += near;
-      or_csweno_limit(m, a, fl, b, eps);
+      or_csweno_limit(&ms, a, fl, b, eps);
       double* t = a; a = b; b = t;
     }
     memcpy(keep, a, n * sizeof(double));
@@ -1406,17 +1481,21 @@ long or_step_gen(const or_mesh* m, double dt, double* u, int ind, double M, int 
   long nf = 0, nn = 0, near = 0, np_ = 0, nb = 0, bad = 0;
   memcpy(un, u, n * sizeof(double));
   const double* prev = un;
+  const double c_in[3] = {0.0, 1.0, 0.5}, c_out[3] = {1.0, 0.5, 1.0};  /* as in or_step */
+  or_mesh ms = *m;
   for (int s = 1; s <= 3; ++s) {
-    or_rk_stage(m, s, dt, un, prev, a);
+    ms.t = m->t + c_in[s - 1] * dt;
+    or_rk_stage(&ms, s, dt, un, prev, a);
+    ms.t = m->t + c_out[s - 1] * dt;
     if (limit) {
-      nf += ind == 2 ? or_flag_kxrcf(m, a, fl, &near, NULL) : or_flag_tvb(m, a, M, fl, &near);
+      nf += ind == 2 ? or_flag_kxrcf(&ms, a, fl, &near, NULL) : or_flag_tvb(&ms, a, M, fl, &near);
       nn += near;
-      if (limit == 2) or_parent_weno_limit(m, a, fl, b, eps);
-      else or_csweno_limit(m, a, fl, b, eps);
+      if (limit == 2) or_parent_weno_limit(&ms, a, fl, b, eps);
+      else or_csweno_limit(&ms, a, fl, b, eps);
       double* t = a; a = b; b = t;
     }
     if (pp) {
-      np_ += or_positivity_limit(m, a, pp_eps, &bad);
+      np_ += or_positivity_limit(&ms, a, pp_eps, &bad);
       nb += bad;
     }
     memcpy(keep, a, n * sizeof(double));
@@ -1481,6 +1560,9 @@ static void ic_eval(int dim, int pde, double gam, int kind, const double* p, dou
     rho = left ? p[0] : p[4] + p[5] * sin(p[6] * x);
     vx = left ? p[1] : p[7];
     pr = left ? p[2] : p[8];
+  } else if (kind == 6) { /* Example 11: post-shock state left of the line x = p8 + p9 y */
+    const int post = x < p[8] + p[9] * y;
+    rho = post ? p[0] : p[4]; vx = post ? p[1] : p[5]; vy = post ? p[2] : p[6]; pr = post ? p[3] : p[7];
   } else if (kind == 5) { /* Example 4: isentropic vortex (exact solution at time p3) */
     const double pi = 3.14159265358979323846;
     double dx = x - p[0] - p[3], dy = y - p[1];

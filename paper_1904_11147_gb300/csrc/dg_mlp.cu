@@ -379,143 +379,128 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-// Scatter of limited modes that first saves the unlimited ones (for the fallback).
-template <int V, int NP>
-__global__ void k_scatter_save(double* __restrict__ Ust, long long ctot, const double* __restrict__ lim,
-                               double* __restrict__ save, long long cap, const int* __restrict__ list_cell,
-                               const Counters* __restrict__ cnt) {
-  const unsigned int n = cnt->n_flag;
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const long long g = list_cell[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v)
-#pragma unroll
-      for (int m = 1; m < NP; ++m) {
-        const long long a = (long long)(v * NP + m) * ctot + g, b = (long long)(v * NP + m) * cap + i;
-        save[b] = Ust[a];
-        Ust[a] = lim[b];
-      }
-  }
-}
-
-// Restores the saved unlimited modes of the listed cells of failing instances.
-template <int V, int NP>
-__global__ void k_restore(double* __restrict__ Ust, long long ctot, const double* __restrict__ save, long long cap,
-                          const int* __restrict__ list_cell, const int* __restrict__ list_inst,
-                          const Counters* __restrict__ cnt, const unsigned int* __restrict__ fail) {
-  const unsigned int n = cnt->n_flag;
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (!fail[list_inst[i]]) continue;
-    const long long g = list_cell[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v)
-#pragma unroll
-      for (int m = 1; m < NP; ++m) Ust[(long long)(v * NP + m) * ctot + g] = save[(long long)(v * NP + m) * cap + i];
-  }
-}
-
-// List C = the entries of list A that belong to failing instances.
-__global__ void k_filter_inst(const int* __restrict__ la_cell, const int* __restrict__ la_inst,
-                              const Counters* __restrict__ cnt_a, const unsigned int* __restrict__ fail, Counters* cnt_c,
-                              int* __restrict__ lc_cell, int* __restrict__ lc_inst) {
-  const unsigned int n = cnt_a->n_flag;
-  const int lane = threadIdx.x & 31;
-  const unsigned int stride = gridDim.x * blockDim.x;
-  for (unsigned int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-    const unsigned int i = base + lane;
-    const bool keep = i < n && fail[la_inst[i]];
-    const unsigned int bal = __ballot_sync(0xffffffffu, keep);
-    unsigned int pos0 = 0;
-    if (lane == 0 && bal) pos0 = atomicAdd(&cnt_c->n_flag, (unsigned)__popc(bal));
-    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-    if (keep) {
-      const unsigned int p = pos0 + __popc(bal & ((1u << lane) - 1u));
-      lc_cell[p] = la_cell[i];
-      lc_inst[p] = la_inst[i];
-    }
-  }
-}
-
 // Positivity screen (Euler): density and pressure at the (N+1)-point Gauss points of the
 // cell and of its faces, evaluated in FP32 from the modes; a point fails when rho <= 0,
-// p <= 1e-6 E (a margin that covers the FP32 rounding of E - |m|^2 / (2 rho)) or a value is
-// not finite.  Sets fail[instance]; with `count`, adds the failing instances to it once.
+// p <= 1e-6 |E| (a margin that covers the FP32 rounding of E - |m|^2 / (2 rho)) or a value
+// is not finite.
 struct PosTab {
   float P[4][4];  // psi_n(x_q), q < N+1
   float P1[4];    // psi_n(1)
   float gm1;
 };
 
-// Screens the listed cells (skip_kept: only the entries the learned filter did not keep,
-// i.e. bit 0 of flags[g] clear) and marks their instances in fail[].
+// True when the cell's density or pressure fails the screen at one of its points.
+template <int DIM, int N>
+__device__ __forceinline__ bool screen_fails(const double* __restrict__ U, long long ctot, long long g,
+                                             const PosTab& tb) {
+  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N), Q = N + 1;
+  float u[V][NP];
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) u[v][m] = d2f_trunc(__ldg(U + (long long)(v * NP + m) * ctot + g));
+  bool bad = false;
+  auto check = [&](const float* q) {
+    const float rho = q[0], E = q[V - 1];
+    float k = q[1] * q[1];
+    if (DIM == 2) k += q[2] * q[2];
+    const float p = tb.gm1 * (E - 0.5f * k / rho);
+    if (!(rho > 0.f) || !(p > 1e-6f * fabsf(E)) || !isfinite(p)) bad = true;
+  };
+  if constexpr (DIM == 1) {
+#pragma unroll
+    for (int q = 0; q < Q + 2; ++q) {
+      float val[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const float b = q < Q ? tb.P[q][m] : ((q == Q || !(m & 1)) ? tb.P1[m] : -tb.P1[m]);
+          s = fmaf(u[v][m], b, s);
+        }
+        val[v] = s;
+      }
+      check(val);
+    }
+  } else {
+    // points: Q x Q volume points, then (r = +-1, s_q) and (r_q, s = +-1)
+#pragma unroll
+    for (int q = 0; q < Q * Q + 4 * Q; ++q) {
+      float val[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const int a = mode_a(m), b = mode_b(m);
+          float fa, fb;
+          if (q < Q * Q) { fa = tb.P[q % Q][a]; fb = tb.P[q / Q][b]; }
+          else {
+            const int f = (q - Q * Q) / Q, j = (q - Q * Q) % Q;
+            const bool minus = (f & 1) != 0;  // faces: +1 then -1
+            if (f < 2) { fa = ((a & 1) && minus) ? -tb.P1[a] : tb.P1[a]; fb = tb.P[j][b]; }
+            else { fa = tb.P[j][a]; fb = ((b & 1) && minus) ? -tb.P1[b] : tb.P1[b]; }
+          }
+          s = fmaf(u[v][m], fa * fb, s);
+        }
+        val[v] = s;
+      }
+      check(val);
+    }
+  }
+  return bad;
+}
+
+// Screens the listed cells and marks the instances of failing ones in fail[].
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) k_positivity_list(const double* __restrict__ U, long long ctot,
                                                          const int* __restrict__ list_cell,
                                                          const int* __restrict__ list_inst,
-                                                         const Counters* __restrict__ cnt,
-                                                         const unsigned char* __restrict__ flags, int skip_kept,
-                                                         PosTab tb, unsigned int* __restrict__ fail) {
-  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N), Q = N + 1;
+                                                         const Counters* __restrict__ cnt, PosTab tb,
+                                                         unsigned int* __restrict__ fail) {
   const unsigned int n = cnt->n_flag;
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const long long g = list_cell[i];
-    if (skip_kept && (flags[g] & 1)) continue;
-    float u[V][NP];
-#pragma unroll
-    for (int v = 0; v < V; ++v)
-#pragma unroll
-      for (int m = 0; m < NP; ++m) u[v][m] = d2f_trunc(__ldg(U + (long long)(v * NP + m) * ctot + g));
-    bool bad = false;
-    auto check = [&](const float* q) {
-      const float rho = q[0], E = q[V - 1];
-      float k = q[1] * q[1];
-      if (DIM == 2) k += q[2] * q[2];
-      const float p = tb.gm1 * (E - 0.5f * k / rho);
-      if (!(rho > 0.f) || !(p > 1e-6f * fabsf(E)) || !isfinite(p)) bad = true;
-    };
-    if constexpr (DIM == 1) {
-#pragma unroll
-      for (int q = 0; q < Q + 2; ++q) {
-        float val[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < NP; ++m) {
-            const float b = q < Q ? tb.P[q][m] : ((q == Q || !(m & 1)) ? tb.P1[m] : -tb.P1[m]);
-            s = fmaf(u[v][m], b, s);
-          }
-          val[v] = s;
-        }
-        check(val);
-      }
-    } else {
-      // points: Q x Q volume points, then (r = +-1, s_q) and (r_q, s = +-1)
-#pragma unroll
-      for (int q = 0; q < Q * Q + 4 * Q; ++q) {
-        float val[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < NP; ++m) {
-            const int a = mode_a(m), b = mode_b(m);
-            float fa, fb;
-            if (q < Q * Q) { fa = tb.P[q % Q][a]; fb = tb.P[q / Q][b]; }
-            else {
-              const int f = (q - Q * Q) / Q, j = (q - Q * Q) % Q;
-              const bool minus = (f & 1) != 0;  // faces: +1 then -1
-              if (f < 2) { fa = ((a & 1) && minus) ? -tb.P1[a] : tb.P1[a]; fb = tb.P[j][b]; }
-              else { fa = tb.P[j][a]; fb = ((b & 1) && minus) ? -tb.P1[b] : tb.P1[b]; }
-            }
-            s = fmaf(u[v][m], fa * fb, s);
-          }
-          val[v] = s;
-        }
-        check(val);
-      }
+    if (screen_fails<DIM, N>(U, ctot, list_cell[i], tb)) atomicOr(fail + list_inst[i], 1u);
+  }
+}
+
+// Positivity gate of the learned indicator: every TVB-listed cell the network skipped
+// (bit 0 of flags[g] clear) whose unlimited state fails the screen is added to the kept
+// list B (warp ballot, one atomic per warp) and to the flags, so that it is limited as
+// the plain method limits it; its instance is marked in fail[] (counted as a fallback).
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) k_positivity_gate(const double* __restrict__ U, long long ctot,
+                                                         const int* __restrict__ la_cell,
+                                                         const int* __restrict__ la_inst,
+                                                         const Counters* __restrict__ cnt_a,
+                                                         unsigned char* __restrict__ flags, PosTab tb,
+                                                         Counters* cnt_b, int* __restrict__ lb_cell,
+                                                         int* __restrict__ lb_inst, unsigned int* __restrict__ fail) {
+  const unsigned int n = cnt_a->n_flag;
+  const int lane = threadIdx.x & 31;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const unsigned int i = base + lane;
+    bool add = false;
+    long long g = 0;
+    int ii = 0;
+    if (i < n) {
+      g = la_cell[i];
+      ii = la_inst[i];
+      add = !(flags[g] & 1) && screen_fails<DIM, N>(U, ctot, g, tb);
     }
-    if (bad) atomicOr(fail + list_inst[i], 1u);
+    const unsigned int bal = __ballot_sync(0xffffffffu, add);
+    unsigned int pos0 = 0;
+    if (lane == 0 && bal) pos0 = atomicAdd(&cnt_b->n_flag, (unsigned)__popc(bal));
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    if (add) {
+      const unsigned int p = pos0 + __popc(bal & ((1u << lane) - 1u));
+      lb_cell[p] = (int)g;
+      lb_inst[p] = ii;
+      flags[g] |= 1;
+      atomicOr(fail + ii, 1u);
+    }
   }
 }
 
@@ -797,42 +782,40 @@ void launch_mlp_filter(int dim, int pde, int N, const LaunchArgs& a, double c0, 
                                    a.us, a.inst, a.ctot, a.bc, c0, W, la_c, la_i, cnt_a, flags, cnt_b, lb_c, lb_i)));
 }
 
-void launch_scatter_save(int dim, int pde, int N, const LaunchArgs& a, const double* lim, double* save, const int* lc,
-                         const Counters* cnt, int nblocks) {
-  DG_DISPATCH_ALL(dim, pde, N, (k_scatter_save<nv_of(D_, P_), np_of(D_, N_)><<<nblocks, 256, 0, a.st>>>(
-                                   a.out, a.ctot, lim, save, a.cap, lc, cnt)));
-}
-
-void launch_restore(int dim, int pde, int N, const LaunchArgs& a, const double* save, const int* lc, const int* li,
-                    const Counters* cnt, const unsigned int* fail, int nblocks) {
-  DG_DISPATCH_ALL(dim, pde, N, (k_restore<nv_of(D_, P_), np_of(D_, N_)><<<nblocks, 256, 0, a.st>>>(
-                                   a.out, a.ctot, save, a.cap, lc, li, cnt, fail)));
-}
-
-void launch_filter_inst(cudaStream_t st, const int* la_c, const int* la_i, const Counters* cnt_a,
-                        const unsigned int* fail, Counters* cnt_c, int* lc_c, int* lc_i, int nblocks) {
-  k_filter_inst<<<nblocks, 256, 0, st>>>(la_c, la_i, cnt_a, fail, cnt_c, lc_c, lc_i);
-}
-
-void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q /* [N+1][N+1] */,
-                            const double* psi_p1, double gam, const int* lc, const int* li, const Counters* cnt,
-                            const unsigned char* flags, int skip_kept, unsigned int* fail, int nblocks) {
+static PosTab pos_tab(int N, const double* psi_q /* [N+1][N+1] */, const double* psi_p1, double gam) {
   PosTab tb{};
   for (int q = 0; q <= N; ++q)
     for (int m = 0; m <= N; ++m) tb.P[q][m] = (float)psi_q[q * (N + 1) + m];
   for (int m = 0; m <= N; ++m) tb.P1[m] = (float)psi_p1[m];
   tb.gm1 = (float)(gam - 1.0);
-#define DG_POS(D, NN) k_positivity_list<D, NN><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, lc, li, cnt, flags, skip_kept, tb, fail)
-  if (dim == 1) {
-    if (N == 1) DG_POS(1, 1);
-    else if (N == 2) DG_POS(1, 2);
-    else DG_POS(1, 3);
-  } else {
-    if (N == 1) DG_POS(2, 1);
-    else if (N == 2) DG_POS(2, 2);
-    else DG_POS(2, 3);
-  }
-#undef DG_POS
+  return tb;
+}
+
+#define DG_POS_DISPATCH(dim, N, CALL)     \
+  do {                                    \
+    if ((dim) == 1) {                     \
+      if ((N) == 1) { constexpr int D_ = 1, N_ = 1; CALL; }      \
+      else if ((N) == 2) { constexpr int D_ = 1, N_ = 2; CALL; } \
+      else { constexpr int D_ = 1, N_ = 3; CALL; }               \
+    } else {                              \
+      if ((N) == 1) { constexpr int D_ = 2, N_ = 1; CALL; }      \
+      else if ((N) == 2) { constexpr int D_ = 2, N_ = 2; CALL; } \
+      else { constexpr int D_ = 2, N_ = 3; CALL; }               \
+    }                                     \
+  } while (0)
+
+void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
+                            const int* lc, const int* li, const Counters* cnt, unsigned int* fail, int nblocks) {
+  const PosTab tb = pos_tab(N, psi_q, psi_p1, gam);
+  DG_POS_DISPATCH(dim, N, (k_positivity_list<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, lc, li, cnt, tb, fail)));
+}
+
+void launch_positivity_gate(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
+                            const int* la_c, const int* la_i, const Counters* cnt_a, unsigned char* flags,
+                            Counters* cnt_b, int* lb_c, int* lb_i, unsigned int* fail, int nblocks) {
+  const PosTab tb = pos_tab(N, psi_q, psi_p1, gam);
+  DG_POS_DISPATCH(dim, N, (k_positivity_gate<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, la_c, la_i, cnt_a, flags,
+                                                                                  tb, cnt_b, lb_c, lb_i, fail)));
 }
 
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total) {

@@ -24,7 +24,10 @@ def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, 
     """Runs the plain method on four-quadrant problems (one per seed) and returns device
     tensors X [S, F] (float32), TVB flags [S] (uint8) and the limiter's relative change [S]
     (float32; zero for unflagged cells).  positivity: apply the positivity-preserving
-    scaling after every stage's limiter (P3 runs lose positivity without it)."""
+    scaling after every stage's limiter and take every step's time step from the wave
+    speeds at the scaling's check points (CFL 0.1), as the batched P3 workload does (P3
+    runs lose positivity without both).  A run whose state stops being finite ends there;
+    samples with non-finite features are dropped."""
     st = stream or torch.cuda.current_stream()
     F = n_features(2, EULER, N)
     xs, fs, ls = [], [], []
@@ -41,11 +44,17 @@ def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, 
         k = 0
         with torch.cuda.stream(st):
             for step in range(steps):
+                if positivity:
+                    sp = m.max_wavespeed(points=True)[0]
+                    dt = 0.1 / max(sp[0] * n + sp[1] * n, 1e-300)
+                    if not math.isfinite(dt):
+                        break
                 for s in (1, 2, 3):
                     m.rk_stage(s, dt)
                     if k % every == 0:
                         m.harvest(X, fl, lab)
                         keep = (fl > 0) | (torch.rand(n * n, device="cuda", generator=gen) < keep_unflagged)
+                        keep &= torch.isfinite(X).all(dim=1) & torch.isfinite(lab)
                         xs.append(X[keep].clone())
                         fs.append(fl[keep].clone())
                         ls.append(lab[keep].clone())
@@ -56,8 +65,6 @@ def harvest_quadrants(seeds, n=96, N=2, steps=120, every=3, keep_unflagged=0.0, 
                         m.positivity_limit()
                     k += 1
         st.synchronize()
-        if not torch.isfinite(xs[-1]).all():
-            raise RuntimeError("non-finite features harvested for seed %d" % seed)
         m.close()
     return torch.cat(xs), torch.cat(fs), torch.cat(ls)
 

@@ -14,6 +14,8 @@ Initial-condition families (``ic`` codes shared with the library's projection ca
   3 density wave:  rho = p0 + p1 sin(p2 x + p3 y), u = p4, v = p5, p = p6
   4 shock/entropy: (rho,u,p) = p0..p2 for x < p3, else rho = p4 + p5 sin(p6 x), u = p7, p = p8
   5 vortex:        isentropic vortex centred at (p0 + p3, p1), strength p2, at time p3
+  6 double Mach:   post-shock (rho,u,v,p) = p0..p3 where x < p8 + p9 y, pre-shock p4..p7
+                   elsewhere (p10: the shock line's speed along x, for the top boundary)
 """
 from __future__ import annotations
 
@@ -25,8 +27,8 @@ import numpy as np
 SEED = 1904
 
 PDE_BURGERS, PDE_EULER = 0, 1
-BC_PERIODIC, BC_OUTFLOW = 0, 1
-IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE, IC_SHOCK_ENTROPY, IC_VORTEX = 0, 1, 2, 3, 4, 5
+BC_PERIODIC, BC_OUTFLOW, BC_DMR = 0, 1, 2
+IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE, IC_SHOCK_ENTROPY, IC_VORTEX, IC_DMR = 0, 1, 2, 3, 4, 5, 6
 GAMMA = 1.4
 
 
@@ -103,6 +105,21 @@ def isentropic_vortex(n: int = 40, N: int = 2) -> Workload:
     periodic, to t = 2 (the domain is our reading; the paper names only the centre)."""
     return Workload("vortex_p%d_%dx%d" % (N, n, n), 2, PDE_EULER, N, [n], [n], [(0.0, 10.0, -5.0, 5.0)],
                     BC_PERIODIC, IC_VORTEX, [[5.0, 0.0, 5.0, 0.0]], 2.0)
+
+
+def double_mach(nx: int = 960, ny: int = 240, N: int = 2) -> Workload:
+    """Example 11: double Mach reflection (Woodward and Colella) on [0,4] x [0,1] to t = 0.2:
+    a Mach 10 shock in air (gamma = 1.4) at 60 degrees to the x axis, its foot at x = 1/6 on
+    the bottom side, running right into gas at rest with rho = 1.4, p = 1.  Post-shock state
+    rho = 8, p = 116.5, velocity 8.25 along the shock normal (cos 30, -sin 30).  The shock
+    line x = 1/6 + y / sqrt(3) moves along x at 20 / sqrt(3) (speed 10 along its normal).
+    Boundaries (BC_DMR): post-shock inflow on the left and on the bottom for x < 1/6, a
+    reflecting wall on the rest of the bottom, outflow on the right, and on the top the
+    post- or pre-shock state on either side of the moving shock."""
+    s3 = math.sqrt(3.0)
+    p = [8.0, 8.25 * s3 / 2.0, -8.25 / 2.0, 116.5, 1.4, 0.0, 0.0, 1.0, 1.0 / 6.0, 1.0 / s3, 20.0 / s3]
+    return Workload("double_mach_p%d_%dx%d" % (N, nx, ny), 2, PDE_EULER, N, [nx], [ny], [(0.0, 4.0, 0.0, 1.0)],
+                    BC_DMR, IC_DMR, [p], 0.2)
 
 
 def quadrant_states(rng) -> list:
