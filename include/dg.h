@@ -46,7 +46,16 @@ typedef enum {
 } dg_status;
 
 typedef enum { DG_BURGERS = 0, DG_EULER = 1 } dg_pde;
-typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1 } dg_bc;
+/* DG_BC_DMR: the boundaries of the double Mach reflection problem (Example 11; 2D Euler
+ * only, data from dg_set_boundary_data): the ghost cell outside a side is decided by its
+ * centre (x_c, y_c) at the time of the state -- left: the post-shock state (inflow); right:
+ * the mirror image of the boundary cell (outflow); bottom: the post-shock state where
+ * x_c < a, else a reflecting wall (mirror image with rho v negated); top: the post-shock
+ * state where x_c < x_s = a + b y_top + c t (the exact position of the moving shock),
+ * else the pre-shock state.  The x side decides first.  Such meshes run the split stage,
+ * the TVB indicator, the CSWENO limiter and the positivity scaling (DG_EINVAL for KXRCF,
+ * the learned indicator and the parent limiter). */
+typedef enum { DG_BC_PERIODIC = 0, DG_BC_OUTFLOW = 1, DG_BC_DMR = 2 } dg_bc;
 typedef enum { DG_IND_TVB = 0, DG_IND_MLP = 1, DG_IND_KXRCF = 2 } dg_indicator;
 typedef enum { DG_LIM_CSWENO = 0, DG_LIM_PARENT = 1 } dg_limiter;
 
@@ -61,14 +70,17 @@ typedef enum { DG_LIM_CSWENO = 0, DG_LIM_PARENT = 1 } dg_limiter;
  *   DG_IC_VORTEX        (2D, Example 4) isentropic vortex centred at (p0 + p3, p1),
  *                       strength p2, at time p3: rho = (1 - (g-1) p2^2 e^{2(1-r^2)} /
  *                       (16 g pi^2))^{1/(g-1)}, u = 1 - p2 e^{1-r^2} (y-p1)/(2 pi),
- *                       v = p2 e^{1-r^2} (x-p0-p3)/(2 pi), p = rho^g               (4) */
+ *                       v = p2 e^{1-r^2} (x-p0-p3)/(2 pi), p = rho^g               (4)
+ *   DG_IC_DMR           (2D, Example 11) post-shock (rho,u,v,p) = p0..p3 where
+ *                       x < p8 + p9 y, pre-shock p4..p7 elsewhere                   (10) */
 typedef enum {
   DG_IC_SINE = 0,
   DG_IC_RIEMANN1D = 1,
   DG_IC_QUADRANT = 2,
   DG_IC_DENSITY_WAVE = 3,
   DG_IC_SHOCK_ENTROPY = 4,
-  DG_IC_VORTEX = 5
+  DG_IC_VORTEX = 5,
+  DG_IC_DMR = 6
 } dg_ic;
 
 /* Create a batch of n_inst meshes sharing dim, PDE, order N and boundary condition.
@@ -183,6 +195,21 @@ dg_status dg_set_positivity(dg_mesh* m, int enable, double eps0);
  * cells whose mean was not admissible (left alone).  Returns DG_EPOSITIVITY when
  * bad_means > 0.  Synchronises the stream. */
 dg_status dg_positivity_counts(dg_mesh* m, int64_t* changed, int64_t* bad_means, int reset);
+
+/* Boundary data of a DG_BC_DMR mesh (Example 11, after Woodward and Colella): p[0..3] the
+ * post-shock (rho, u, v, p), p[4..7] the pre-shock state, p[8..10] a, b, c of the shock
+ * line x_s(y, t) = a + b y + c t (a is also where the wall starts on the bottom side).
+ * n must be 11.  Required before the first stage.  Synchronises the stream.  Errors:
+ * DG_EINVAL (another bc, n != 11, non-positive density or pressure). */
+dg_status dg_set_boundary_data(dg_mesh* m, const double* p, int n);
+
+/* Time of u^n per instance (host array of n_inst doubles; 0 at creation) for the
+ * time-dependent boundaries of DG_BC_DMR meshes.  The stages evaluate the boundaries at
+ * the SSP-RK3 stage times t, t + dt, t + dt/2; the indicator and the limiter after stage s
+ * at the time of its output (t + dt, t + dt/2, t + dt); stage 3 advances t by dt.
+ * dg_get_time reads it back (synchronises).  Errors: DG_EINVAL (another bc). */
+dg_status dg_set_time(dg_mesh* m, const double* t);
+dg_status dg_get_time(dg_mesh* m, double* t);
 
 /* One full SSP-RK3 step: three times (stage, indicator, limiter), replayed from a CUDA
  * graph captured on the first call.  dt as in dg_rk_stage. */

@@ -17,10 +17,11 @@ LIB_PATH = os.path.join(HERE, "libcswenodg.so")
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_EPOSITIVITY, DG_ETIMEOUT, DG_ESTATE = range(7)
 BURGERS, EULER = 0, 1
-BC_PERIODIC, BC_OUTFLOW = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_DMR = 0, 1, 2
 IND_TVB, IND_MLP, IND_KXRCF = 0, 1, 2
 LIM_CSWENO, LIM_PARENT = 0, 1
 IC_SINE, IC_RIEMANN1D, IC_QUADRANT, IC_DENSITY_WAVE = 0, 1, 2, 3
+IC_DMR = 6
 STATUS_NAMES = {0: "DG_OK", 1: "DG_EINVAL", 2: "DG_ENOMEM", 3: "DG_ECUDA", 4: "DG_EPOSITIVITY",
                 5: "DG_ETIMEOUT", 6: "DG_ESTATE"}
 
@@ -85,6 +86,12 @@ def lib():
             l.dg_autotune.restype = ctypes.c_int
             l.dg_indicator_logits.argtypes = [P, P]
             l.dg_refined_arith.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
+            l.dg_set_boundary_data.argtypes = [P, D, ctypes.c_int]
+            l.dg_set_boundary_data.restype = ctypes.c_int
+            l.dg_set_time.argtypes = [P, D]
+            l.dg_set_time.restype = ctypes.c_int
+            l.dg_get_time.argtypes = [P, D]
+            l.dg_get_time.restype = ctypes.c_int
             l.dg_refined_arith.restype = ctypes.c_int
             l.dg_harvest.argtypes = [P, ctypes.c_double, P, P, P]
             l.dg_positivity_limit.argtypes = [P, ctypes.c_double]
@@ -199,6 +206,21 @@ class Mesh:
     def set_dt(self, dt):
         d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.n_inst,)))
         _check(lib().dg_set_dt(self._h, _dp(d)))
+
+    def set_boundary_data(self, p):
+        """dg_set_boundary_data (BC_DMR meshes): post-shock and pre-shock (rho, u, v, p), then
+        a, b, c of the shock line x_s(y, t) = a + b y + c t."""
+        a = np.ascontiguousarray(p, dtype=np.float64)
+        _check(lib().dg_set_boundary_data(self._h, _dp(a), a.size))
+
+    def set_time(self, t):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), (self.n_inst,)))
+        _check(lib().dg_set_time(self._h, _dp(d)))
+
+    def get_time(self):
+        d = np.zeros(self.n_inst)
+        _check(lib().dg_get_time(self._h, _dp(d)))
+        return d
 
     # -- the method ----------------------------------------------------------------------
     def rk_stage(self, stage, dt):

@@ -209,6 +209,10 @@ struct dg_mesh {
   int limiter = DG_LIM_CSWENO;
   int g_lim = -1;
   int min_side = 1;  // smallest instance side (the parent stencil needs N+1 cells)
+  // double Mach reflection boundaries (DG_BC_DMR): data and per-instance times on the
+  // device (layout in dg_shared.cuh), and whether dg_set_boundary_data was called
+  double* d_bcd = nullptr;
+  bool bcd_set = false;
 };
 
 static size_t mesh_doubles(const dg_mesh* m) { return (size_t)m->ncell * m->V * m->NP; }
@@ -237,6 +241,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_speed);
   cudaFree(m->flag_totals);
   cudaFree(m->mlp_buf);
+  cudaFree(m->d_bcd);
   cudaFree(m->lb_cell); cudaFree(m->lb_inst);
   cudaFree(m->cnt_b); cudaFree(m->fail); cudaFree(m->pos_counts);
   cudaFree(m->pp_counts);
@@ -315,7 +320,9 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (pde != DG_BURGERS && pde != DG_EULER) return fail(DG_EINVAL, "unknown pde %d", pde);
   if (N < 1 || N > 3) return fail(DG_EINVAL, "order N must be 1..3 (got %d)", N);
   if (n_inst < 1 || !nx || !box || (dim == 2 && !ny)) return fail(DG_EINVAL, "bad instance arrays");
-  if (bc != DG_BC_PERIODIC && bc != DG_BC_OUTFLOW) return fail(DG_EINVAL, "unknown bc %d", bc);
+  if (bc != DG_BC_PERIODIC && bc != DG_BC_OUTFLOW && bc != DG_BC_DMR) return fail(DG_EINVAL, "unknown bc %d", bc);
+  if (bc == DG_BC_DMR && (dim != 2 || pde != DG_EULER))
+    return fail(DG_EINVAL, "the double Mach reflection boundaries are for 2D Euler meshes");
   if (pde == DG_EULER && !(gamma > 1.0)) return fail(DG_EINVAL, "gamma must exceed 1");
   dg_status s = dg_ensure_tables_internal();
   if (s != DG_OK) return s;
@@ -380,7 +387,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst) &&
             alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long)) &&
             alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long)) &&
-            alloc((void**)&m->d_kx_hpow, sizeof(double) * n_inst);
+            alloc((void**)&m->d_kx_hpow, sizeof(double) * n_inst) &&
+            (bc != DG_BC_DMR || alloc((void**)&m->d_bcd, sizeof(double) * (kDmrInst + kDmrStride * n_inst)));
   if (!ok) {
     cudaGetLastError();
     dg_mesh_destroy(m);
@@ -393,6 +401,11 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
   if (e == cudaSuccess) e = cudaMemset(m->cnt, 0, sizeof(Counters));
   if (e == cudaSuccess) e = cudaMemset(m->flag_totals, 0, 3 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(m->pp_counts, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess && bc == DG_BC_DMR) {  // times 0, the top side's y per instance; data set later
+    std::vector<double> bcd(kDmrInst + kDmrStride * n_inst, 0.0);
+    for (int i = 0; i < n_inst; ++i) bcd[kDmrInst + kDmrStride * i + 1] = box[4 * i + 3];
+    e = cudaMemcpy(m->d_bcd, bcd.data(), sizeof(double) * bcd.size(), cudaMemcpyHostToDevice);
+  }
   {
     std::vector<double> hp(n_inst);
     for (int i = 0; i < n_inst; ++i) {
@@ -467,6 +480,10 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
       m->d_face_tiles = nullptr;
       m->stage_split = false;
     }
+    if (bc == DG_BC_DMR && !m->fbuf) {
+      dg_mesh_destroy(m);
+      return fail(DG_ENOMEM, "the double Mach reflection boundaries need the split stage's face planes");
+    }
   }
   *out = m;
   return DG_OK;
@@ -489,10 +506,48 @@ static L args(dg_mesh* m, int un, int us, int out) {
   a.bc = m->bc;
   a.gam = m->gamma;
   a.lq = m->d_lq;
+  a.bcd = m->d_bcd;
   return a;
 }
 
+// Times of the kBcDmr boundary data after stage s of SSP-RK3: the output of stage 1 holds at
+// t^n + dt, of stage 2 at t^n + dt/2, of stage 3 at t^n + dt, which becomes the new t^n.
+// kBcDmr meshes run the stage, the TVB indicator, the CSWENO limiter and the positivity
+// scaling; the other indicators and limiters have no double Mach reflection ghosts.
+static dg_status dmr_check(const dg_mesh* m, int indicator) {
+  if (m->bc != DG_BC_DMR) return DG_OK;
+  if (!m->bcd_set) return fail(DG_ESTATE, "set the boundary data (dg_set_boundary_data) first");
+  if (indicator != DG_IND_TVB)
+    return fail(DG_EINVAL, "the double Mach reflection boundaries support the TVB indicator only");
+  return DG_OK;
+}
+
+static __global__ void k_stage_time(double* __restrict__ bcd, const Inst* __restrict__ insts, int n_inst, int stage,
+                                    double dt_all) {
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    double* ti = bcd + kDmrInst + kDmrStride * i;
+    const double dt = dt_all > 0.0 ? dt_all : insts[i].dt;
+    if (stage == 0) {  // the current state is u^n again (dg_set_modes)
+      ti[0] = ti[2];
+      continue;
+    }
+    const double c = stage == 2 ? 0.5 : 1.0;
+    ti[0] = ti[2] + c * dt;
+    if (stage == 3) ti[2] = ti[0];
+  }
+}
+
 static void k_stage(dg_mesh* m, int stage, int in, int out, double dt_all) {
+  if (m->bc == DG_BC_DMR) {
+    // the stage evaluates L at the time of its input state (bcd), then the times advance
+    LaunchArgs a = args<LaunchArgs>(m, 0, in, out);
+    double* fy = m->fbuf + (size_t)(m->N + 1) * m->V * m->fxt;
+    launch_stage2_split(m->pde, m->N, a, stage, dt_all, m->d_face_tiles, m->n_face_tiles, m->fbuf, m->fxt, fy,
+                        m->fyt);
+    k_stage_time<<<1, 32, 0, m->st>>>(m->d_bcd, m->d_inst, m->n_inst, stage, dt_all);
+    m->launches += 3;
+    return;
+  }
   if (m->dim == 1) {
     launch_stage1(m->pde, m->N, args<LaunchArgs>(m, 0, in, out), stage, dt_all);
   } else {
@@ -673,6 +728,10 @@ extern "C" dg_status dg_set_modes(dg_mesh* m, const double* modes, size_t n, int
   const int nb = (int)std::min<long long>((m->ncell + 255) / 256, 65535);
   k_aos_to_soa<<<nb, 256, 0, m->st>>>(src, m->U[0], m->ncell, m->ctot, vn);
   m->launches++;
+  if (m->bc == DG_BC_DMR) {
+    k_stage_time<<<1, 32, 0, m->st>>>(m->d_bcd, m->d_inst, m->n_inst, 0, 0.0);
+    m->launches++;
+  }
   CK(cudaGetLastError());
   invalidate(m);
   return DG_OK;
@@ -694,8 +753,8 @@ extern "C" dg_status dg_get_modes(dg_mesh* m, double* out, size_t n, int is_devi
 
 extern "C" dg_status dg_project_ic(dg_mesh* m, int ic, const double* params, int nparams) {
   if (!m || !params) return fail(DG_EINVAL, "null argument");
-  static const int need[6] = {4, 7, 18, 7, 9, 4};
-  if (ic < 0 || ic > 5) return fail(DG_EINVAL, "unknown initial condition %d", ic);
+  static const int need[7] = {4, 7, 18, 7, 9, 4, 10};
+  if (ic < 0 || ic > 6) return fail(DG_EINVAL, "unknown initial condition %d", ic);
   if (nparams < need[ic]) return fail(DG_EINVAL, "initial condition %d needs %d parameters", ic, need[ic]);
   if ((m->pde == DG_BURGERS) != (ic == DG_IC_SINE)) return fail(DG_EINVAL, "initial condition does not fit the PDE");
   if ((ic == DG_IC_RIEMANN1D || ic == DG_IC_SHOCK_ENTROPY) && m->dim != 1)
@@ -737,6 +796,7 @@ static dg_status check_dt(dg_mesh* m, double dt) {
 static int stage_out(int s) { return s == 1 ? 1 : (s == 2 ? 2 : 0); }
 
 extern "C" dg_status dg_rk_stage(dg_mesh* m, int stage, double dt) {
+  if (m && m->bc == DG_BC_DMR && !m->bcd_set) return fail(DG_ESTATE, "set the boundary data (dg_set_boundary_data) first");
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (stage < 1 || stage > 3) return fail(DG_EINVAL, "stage must be 1..3 (got %d)", stage);
   if (m->last_stage != stage - 1 && !(stage == 1 && m->last_stage == 3))
@@ -754,6 +814,10 @@ extern "C" dg_status dg_rk_stage(dg_mesh* m, int stage, double dt) {
 
 extern "C" dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flagged, int64_t* n_near,
                                    uint8_t* flags_out) {
+  if (m) {
+    dg_status ds = dmr_check(m, indicator);
+    if (ds != DG_OK) return ds;
+  }
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (indicator != DG_IND_TVB && indicator != DG_IND_MLP && indicator != DG_IND_KXRCF)
     return fail(DG_EINVAL, "unknown indicator %d", indicator);
@@ -795,6 +859,7 @@ extern "C" dg_status dg_cswenolimit(dg_mesh* m) {
 }
 
 extern "C" dg_status dg_parent_wenolimit(dg_mesh* m) {
+  if (m && m->bc == DG_BC_DMR) return fail(DG_EINVAL, "not available with the double Mach reflection boundaries");
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (!m->flags_valid) return fail(DG_ESTATE, "no troubled-cell flags for the current state");
   if (m->min_side < m->N + 1) return fail(DG_EINVAL, "the parent WENO stencil needs %d cells per side", m->N + 1);
@@ -806,6 +871,8 @@ extern "C" dg_status dg_parent_wenolimit(dg_mesh* m) {
 }
 
 extern "C" dg_status dg_set_limiter(dg_mesh* m, int limiter) {
+  if (m && m->bc == DG_BC_DMR && limiter != DG_LIM_CSWENO)
+    return fail(DG_EINVAL, "the double Mach reflection boundaries support the CSWENO limiter only");
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (limiter != DG_LIM_CSWENO && limiter != DG_LIM_PARENT) return fail(DG_EINVAL, "unknown limiter %d", limiter);
   if (limiter == DG_LIM_PARENT && m->min_side < m->N + 1)
@@ -896,8 +963,56 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_set_boundary_data(dg_mesh* m, const double* p, int n) {
+  if (!m || !p) return fail(DG_EINVAL, "null argument");
+  if (m->bc != DG_BC_DMR) return fail(DG_EINVAL, "the mesh has no boundary data (bc %d)", m->bc);
+  if (n != 11) return fail(DG_EINVAL, "the double Mach reflection boundaries take 11 values (got %d)", n);
+  double h[kDmrInst];
+  for (int k = 0; k < 2; ++k) {
+    const double rho = p[4 * k], u = p[4 * k + 1], v = p[4 * k + 2], pr = p[4 * k + 3];
+    if (!(rho > 0.0) || !(pr > 0.0)) return fail(DG_EINVAL, "boundary states need positive density and pressure");
+    double* c = h + (k == 0 ? kDmrPost : kDmrPre);
+    c[0] = rho;
+    c[1] = rho * u;
+    c[2] = rho * v;
+    c[3] = pr / (m->gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+  }
+  h[kDmrA] = p[8];
+  h[kDmrB] = p[9];
+  h[kDmrC] = p[10];
+  CK(cudaMemcpyAsync(m->d_bcd, h, sizeof(h), cudaMemcpyHostToDevice, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  m->bcd_set = true;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_set_time(dg_mesh* m, const double* t) {
+  if (!m || !t) return fail(DG_EINVAL, "null argument");
+  if (m->bc != DG_BC_DMR) return fail(DG_EINVAL, "only meshes with time-dependent boundaries keep a time");
+  const size_t pitch = sizeof(double) * kDmrStride;
+  CK(cudaMemcpy2DAsync(m->d_bcd + kDmrInst + 2, pitch, t, sizeof(double), sizeof(double), m->n_inst,
+                       cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemcpy2DAsync(m->d_bcd + kDmrInst, pitch, t, sizeof(double), sizeof(double), m->n_inst,
+                       cudaMemcpyHostToDevice, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_get_time(dg_mesh* m, double* t) {
+  if (!m || !t) return fail(DG_EINVAL, "null argument");
+  if (m->bc != DG_BC_DMR) return fail(DG_EINVAL, "only meshes with time-dependent boundaries keep a time");
+  CK(cudaMemcpy2DAsync(t, sizeof(double), m->d_bcd + kDmrInst + 2, sizeof(double) * kDmrStride, sizeof(double),
+                       m->n_inst, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return DG_OK;
+}
+
 extern "C" dg_status dg_step(dg_mesh* m, double dt, int indicator, double tvb_M) {
   if (!m) return fail(DG_EINVAL, "null mesh");
+  {
+    dg_status ds = dmr_check(m, indicator);
+    if (ds != DG_OK) return ds;
+  }
   if (indicator != DG_IND_TVB && indicator != DG_IND_MLP && indicator != DG_IND_KXRCF)
     return fail(DG_EINVAL, "unknown indicator %d", indicator);
   if (indicator == DG_IND_MLP && !m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
@@ -990,6 +1105,7 @@ extern "C" dg_status dg_autotune(dg_mesh* m, double dt, int* stage_ty, int* limi
     }
     m->stage_split = false;
     for (int ty : {8, 4}) {
+      if (m->bc == DG_BC_DMR) break;  // the boundary data are read by the split stage only
       cudaError_t e = build_stage_tiles(m, ty);
       if (e != cudaSuccess) return fail(DG_ECUDA, "stage tiles: %s", cudaGetErrorString(e));
       for (int pers : {0, 1}) {
@@ -1244,6 +1360,7 @@ extern "C" dg_status dg_mlp_predict(dg_mlp* n, const float* X, int64_t B, float*
 }
 
 extern "C" dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau) {
+  if (m && m->bc == DG_BC_DMR) return fail(DG_EINVAL, "not available with the double Mach reflection boundaries");
   if (!m || !n) return fail(DG_EINVAL, "null argument");
   const int F = mlp_features(m->dim, m->pde, m->N);
   if (F != n->F) return fail(DG_EINVAL, "network has %d features, this mesh needs %d", n->F, F);
@@ -1305,6 +1422,7 @@ extern "C" dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_
 }
 
 extern "C" dg_status dg_indicator_logits(dg_mesh* m, float* logits) {
+  if (m && m->bc == DG_BC_DMR) return fail(DG_EINVAL, "not available with the double Mach reflection boundaries");
   if (!m || !logits) return fail(DG_EINVAL, "null argument");
   if (!m->has_mlp) return fail(DG_EINVAL, "no learned indicator attached to the mesh");
   CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
@@ -1325,6 +1443,7 @@ extern "C" dg_status dg_refined_arith(int op, const double* x, double* out, int6
 }
 
 extern "C" dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* change) {
+  if (m && m->bc == DG_BC_DMR) return fail(DG_EINVAL, "not available with the double Mach reflection boundaries");
   if (!m || !X || !flags || !change) return fail(DG_EINVAL, "null argument");
   LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
   const double c0 = mean_factor(m);

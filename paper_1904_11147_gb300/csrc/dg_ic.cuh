@@ -11,6 +11,8 @@
 //                              rho = (1 - (g-1) p2^2 e^(2(1-r^2)) / (16 g pi^2))^(1/(g-1)),
 //                              u = 1 - p2 e^(1-r^2) (y - p1) / (2 pi),
 //                              v = p2 e^(1-r^2) (x - p0 - p3) / (2 pi), p = rho^g
+//   6 double Mach (2D):        post-shock (rho,u,v,p) = p0..p3 where x < p8 + p9 y, the
+//                              pre-shock state p4..p7 elsewhere (Example 11)
 #pragma once
 
 namespace dg {
@@ -40,6 +42,9 @@ __device__ __forceinline__ void ic_eval2(int kind, const double* p, double x, do
   if (kind == 2) {
     const int q = (x >= p[16]) ? (y >= p[17] ? 0 : 3) : (y >= p[17] ? 1 : 2);
     rho = p[4 * q]; vx = p[4 * q + 1]; vy = p[4 * q + 2]; pr = p[4 * q + 3];
+  } else if (kind == 6) {
+    const bool post = x < __dadd_rn(p[8], __dmul_rn(p[9], y));  // as the oracle rounds it
+    rho = post ? p[0] : p[4]; vx = post ? p[1] : p[5]; vy = post ? p[2] : p[6]; pr = post ? p[3] : p[7];
   } else if (kind == 5) {
     const double pi = 3.14159265358979323846;
     const double dx = x - p[0] - p[3], dy = y - p[1];

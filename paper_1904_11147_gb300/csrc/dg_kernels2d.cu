@@ -183,6 +183,35 @@ __device__ __forceinline__ void load_cell(const double* __restrict__ U, long lon
     }
 }
 
+// load_cell with the kBcDmr ghosts (dmr_ghost) for cells outside instance `inst`.
+// t: the time of the state U.
+template <int V, int NP>
+__device__ __forceinline__ void load_cell_bc(const double* __restrict__ U, long long ctot, const Inst& I, int inst,
+                                             int ix, int iy, int bc, const double* __restrict__ bcd, double t,
+                                             double (&u)[V][NP]) {
+  if (bc != kBcDmr || (ix >= 0 && ix < I.nx && iy >= 0 && iy < I.ny)) {
+    load_cell<V, NP>(U, ctot, I, ix, iy, bc, u);
+    return;
+  }
+  const Ghost gh = dmr_ghost(I, inst, ix, iy, bcd, t);
+  if (gh.c) {  // constant state: U_00 = mean / psi_0^2 = 2 mean, no other mode
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int m = 0; m < NP; ++m) u[v][m] = m == 0 ? 2.0 * gh.c[v] : 0.0;
+    return;
+  }
+  const long long g = I.off + (long long)gh.jy * I.nx + gh.jx;
+#pragma unroll
+  for (int v = 0; v < V; ++v)
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      const double x = __ldg(U + (long long)(v * NP + m) * ctot + g);
+      const bool flip = ((gh.fx && (mode_a(m) & 1)) != (gh.fy && (mode_b(m) & 1))) != (gh.fv && v == 2);
+      u[v][m] = neg_if(x, flip);
+    }
+}
+
 // Traces on the east (r = +1) and west (r = -1) faces at the Q face points:
 // u(+-1, s_q) = sum_b psi_b(s_q) sum_a (+-1)^a U_ab psi_a(1).
 template <int N, int V, int NP>
@@ -649,7 +678,8 @@ template <int PDE, int N>
 __global__ void __launch_bounds__(128) k_face2(const double* __restrict__ us, const Inst* __restrict__ insts,
                                                const Tile* __restrict__ tiles, long long ctot, int bc, double gam,
                                                double* __restrict__ fx, long long fxt, double* __restrict__ fy,
-                                               long long fyt) {
+                                               long long fyt, const double* __restrict__ bcd, int stage,
+                                               double dt_all) {
   using O = Off<N>;
   constexpr int V = nv_of(2, PDE), NP = np_of(2, N), Q = N + 1;
   const Tile tile = tiles[blockIdx.x];
@@ -658,15 +688,18 @@ __global__ void __launch_bounds__(128) k_face2(const double* __restrict__ us, co
   const int k = tile.x0 + (threadIdx.x & 31), j = tile.y0 + (threadIdx.x >> 5);
   if (dir == 0 ? (k > I.nx || j >= I.ny) : (k >= I.nx || j > I.ny)) return;
   const double gm1 = gam - 1.0;
+  // kBcDmr: the stage's input holds at t^n, t^n + dt, t^n + dt/2 for stages 1, 2, 3
+  double t_in = 0.0;
+  if (bc == kBcDmr) t_in = dmr_time(bcd, tile.inst, 2) + (stage == 1 ? 0.0 : (stage == 2 ? 1.0 : 0.5)) * (dt_all > 0.0 ? dt_all : I.dt);
   double tL[Q][V], tR[Q][V];
   {
     double u[V][NP];
-    load_cell<V, NP>(us, ctot, I, dir == 0 ? k - 1 : k, dir == 0 ? j : j - 1, bc, u);
+    load_cell_bc<V, NP>(us, ctot, I, tile.inst, dir == 0 ? k - 1 : k, dir == 0 ? j : j - 1, bc, bcd, t_in, u);
     face_trace2<N>(u, dir, false, tL);
   }
   {
     double u[V][NP];
-    load_cell<V, NP>(us, ctot, I, k, j, bc, u);
+    load_cell_bc<V, NP>(us, ctot, I, tile.inst, k, j, bc, bcd, t_in, u);
     face_trace2<N>(u, dir, true, tR);
   }
   double G[Q][V];
@@ -986,7 +1019,7 @@ template <int PDE, int N>
 __global__ void __launch_bounds__(256)
     k_flag2(const double* __restrict__ U, const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
             long long ctot, int bc, double M, unsigned char* __restrict__ flags, Counters* cnt,
-            int* __restrict__ list_cell, int* __restrict__ list_inst) {
+            int* __restrict__ list_cell, int* __restrict__ list_inst, const double* __restrict__ bcd) {
   using O = Off<N>;
   constexpr int V = nv_of(2, PDE), NP = np_of(2, N);
   const Tile tile = tiles[blockIdx.x];
@@ -994,11 +1027,19 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ix = tile.x0 + lane, iy = tile.y0 + w;
   const bool active = ix < I.nx && iy < I.ny;
+  const double c00 = T(O::C00);
   int fl = 0;
   bool near = false;
-  long long g = 0;
+  long long g = active ? I.off + (long long)iy * I.nx + ix : 0;
+  // every cell's means go to shared memory once; the neighbours inside the tile read them
+  // there, those outside it (and ghosts) form them from their U_00 as before
+  __shared__ double s_mean[V][TY][TX];
   if (active) {
-    g = I.off + (long long)iy * I.nx + ix;
+#pragma unroll
+    for (int v = 0; v < V; ++v) s_mean[v][w][lane] = __dmul_rn(__ldg(U + (long long)(v * NP) * ctot + g), c00);
+  }
+  __syncthreads();
+  if (active) {
     // neighbour cells (outflow ghosts have the boundary cell's mean)
     auto nb = [&](int jx, int jy) -> long long {
       if (bc == 0) {
@@ -1011,28 +1052,54 @@ __global__ void __launch_bounds__(256)
       return I.off + (long long)jy * I.nx + jx;
     };
     const long long gW = nb(ix - 1, iy), gE = nb(ix + 1, iy), gS = nb(ix, iy - 1), gN = nb(ix, iy + 1);
-    const double c00 = T(O::C00);
+    const bool inW = lane > 0, inE = lane < TX - 1 && ix + 1 < I.nx;
+    const bool inS = w > 0, inN = w < TY - 1 && iy + 1 < I.ny;
+    // kBcDmr: the neighbours' U_00 (W, E, S, N) follow dmr_ghost where they lie outside
+    Ghost gh[4];
+    const bool dmr = bc == kBcDmr && (ix == 0 || iy == 0 || ix == I.nx - 1 || iy == I.ny - 1);
+    if (dmr) {
+      const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int jx = ix + ox[k], jy = iy + oy[k];
+        const bool out = jx < 0 || jx >= I.nx || jy < 0 || jy >= I.ny;
+        gh[k] = out ? dmr_ghost(I, tile.inst, jx, jy, bcd, dmr_time(bcd, tile.inst, 0))
+                    : Ghost{nullptr, jx, jy, false, false, false};
+      }
+    }
+    auto nb_u00 = [&](int k, const double* P, long long gk, int v) -> double {
+      if (!dmr) return __ldg(P + gk);
+      if (gh[k].c) return 2.0 * gh[k].c[v];
+      return neg_if(__ldg(P + I.off + (long long)gh[k].jy * I.nx + gh[k].jx), gh[k].fv && v == 2);
+    };
     const long long mx2 = __double_as_longlong(M * I.hx * I.hx), my2 = __double_as_longlong(M * I.hy * I.hy);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const double* P = U + (long long)(v * NP) * ctot;
-      const double mean = __dmul_rn(__ldg(P + g), c00);
-      const double mW = __dmul_rn(__ldg(P + gW), c00), mE = __dmul_rn(__ldg(P + gE), c00);
-      const double mS = __dmul_rn(__ldg(P + gS), c00), mN = __dmul_rn(__ldg(P + gN), c00);
+      const double mean = s_mean[v][w][lane];
+      const double mW = inW ? s_mean[v][w][lane - 1] : __dmul_rn(nb_u00(0, P, gW, v), c00);
+      const double mE = inE ? s_mean[v][w][lane + 1] : __dmul_rn(nb_u00(1, P, gE, v), c00);
+      const double mS = inS ? s_mean[v][w - 1][lane] : __dmul_rn(nb_u00(2, P, gS, v), c00);
+      const double mN = inN ? s_mean[v][w + 1][lane] : __dmul_rn(nb_u00(3, P, gN, v), c00);
+      // the serial sums start from their first term (0 + x = x up to the sign of a zero,
+      // which no decision below depends on)
       double uE = 0.0, uW = 0.0, uN = 0.0, uS = 0.0;
+      bool firstE = true, firstN = true;
 #pragma unroll
       for (int m = 0; m < NP; ++m) {
         const int a = mode_a(m), b = mode_b(m);
         const double ck = __ldg(P + (long long)m * ctot + g);
         if (!(b & 1)) {  // psi_b(0) != 0: east/west products (west = (-1)^a east)
           const double pe = __dmul_rn(ck, T(O::TE + m));
-          uE = __dadd_rn(uE, pe);
-          uW = (a & 1) ? __dsub_rn(uW, pe) : __dadd_rn(uW, pe);
+          uE = firstE ? pe : __dadd_rn(uE, pe);
+          uW = firstE ? ((a & 1) ? -pe : pe) : ((a & 1) ? __dsub_rn(uW, pe) : __dadd_rn(uW, pe));
+          firstE = false;
         }
         if (!(a & 1)) {  // psi_a(0) != 0: north/south products (south = (-1)^b north)
           const double pn = __dmul_rn(ck, T(O::TN + m));
-          uN = __dadd_rn(uN, pn);
-          uS = (b & 1) ? __dsub_rn(uS, pn) : __dadd_rn(uS, pn);
+          uN = firstN ? pn : __dadd_rn(uN, pn);
+          uS = firstN ? ((b & 1) ? -pn : pn) : ((b & 1) ? __dsub_rn(uS, pn) : __dadd_rn(uS, pn));
+          firstN = false;
         }
       }
       const double dpx = __dsub_rn(mE, mean), dmx = __dsub_rn(mean, mW);
@@ -1302,7 +1369,7 @@ __global__ void __launch_bounds__(128)
     k_limit2_euler_quad(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc,
                         const int* __restrict__ list_cell, const int* __restrict__ list_inst,
                         const Counters* __restrict__ cnt, double* __restrict__ lim, long long cap, double gam,
-                        unsigned int* __restrict__ lq) {
+                        unsigned int* __restrict__ lq, const double* __restrict__ bcd) {
   using O = Off<N>;
   constexpr int NP = np_of(2, N), NS = O::NS, NG = O::NG, N1 = N + 1;
   const unsigned int n = cnt->n_flag;
@@ -1323,7 +1390,8 @@ __global__ void __launch_bounds__(128)
     const bool active = i0 < n;
     const unsigned int i = active ? i0 : n - 1;  // idle quads repeat a valid entry
     const long long g = list_cell[i];
-    const Inst I = insts[list_inst[i]];
+    const int inst = list_inst[i];
+    const Inst I = insts[inst];
     const int loc = (int)(g - I.off);
     const int ix = loc % I.nx, iy = loc / I.nx;
     // subcell averages of variable q
@@ -1333,10 +1401,20 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         int jx = ix + dx, jy = iy + dy;
-        bool fx = false, fy = false;
+        bool fx = false, fy = false, fv = false;
+        const double* cst = nullptr;  // kBcDmr constant ghost
         if (bc == 0) {
           jx = jx < 0 ? jx + I.nx : (jx >= I.nx ? jx - I.nx : jx);
           jy = jy < 0 ? jy + I.ny : (jy >= I.ny ? jy - I.ny : jy);
+        } else if (bc == kBcDmr && (jx < 0 || jx >= I.nx || jy < 0 || jy >= I.ny)) {
+          const Ghost gh = dmr_ghost(I, inst, jx, jy, bcd, dmr_time(bcd, inst, 0));
+          cst = gh.c;
+          jx = gh.jx;
+          jy = gh.jy;
+          fx = gh.fx;
+          fy = gh.fy;
+          fv = gh.fv && q == 2;
+          if (cst) { jx = 0; jy = 0; }
         } else {
           if (jx < 0) { jx = 0; fx = true; }
           if (jx >= I.nx) { jx = I.nx - 1; fx = true; }
@@ -1348,8 +1426,9 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
           const double x = __ldg(U + (long long)(q * NP + m) * ctot + gj);
-          const bool flip = (fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1));
+          const bool flip = ((fx && (mode_a(m) & 1)) != (fy && (mode_b(m) & 1))) != fv;
           u[m] = neg_if(x, flip);
+          if (cst) u[m] = m == 0 ? 2.0 * cst[q] : 0.0;
         }
         constexpr int k0[3] = {0, N, N + 1};
         constexpr int kn[3] = {N, 1, N};
@@ -1590,7 +1669,8 @@ static constexpr size_t cell_smem2(int pde, int N) {
 void launch_stage2_split(int pde, int N, const LaunchArgs& a, int stage, double dt_all, const Tile* face_tiles,
                          int nface_tiles, double* fx, long long fxt, double* fy, long long fyt) {
   DG_DISPATCH2(pde, N, (k2::k_face2<P_, N_><<<nface_tiles, 128, 0, a.st>>>(a.us, a.inst, face_tiles, a.ctot, a.bc,
-                                                                            a.gam, fx, fxt, fy, fyt)));
+                                                                            a.gam, fx, fxt, fy, fyt, a.bcd, stage,
+                                                                            dt_all)));
   DG_DISPATCH2(pde, N, (k2::k_cell2<P_, N_><<<a.ntiles, 256, cell_smem2(P_, N_), a.st>>>(a.un, a.us, a.out, a.inst, a.tiles, a.ctot,
                                                                          stage, dt_all, fx, fxt, fy, fyt, a.gam)));
 }
@@ -1607,16 +1687,16 @@ void launch_stage2(int pde, int N, const LaunchArgs& a, int stage, double dt_all
 void launch_flag2(int pde, int N, const LaunchArgs& a, double M, unsigned char* flags, Counters* cnt, int* lc,
                   int* li) {
   DG_DISPATCH2(pde, N, (k2::k_flag2<P_, N_><<<a.ntiles, 256, 0, a.st>>>(a.us, a.inst, a.tiles, a.ctot, a.bc, M,
-                                                                          flags, cnt, lc, li)));
+                                                                          flags, cnt, lc, li, a.bcd)));
 }
 
 void launch_limit2(int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
                    double* lim, int nblocks) {
   if (pde == 1) {  // Euler: four lanes per troubled cell
     if (a.lq) cudaMemsetAsync(a.lq, 0, sizeof(unsigned int), a.st);
-    if (N == 1) k2::k_limit2_euler_quad<1><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
-    else if (N == 2) k2::k_limit2_euler_quad<2><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
-    else k2::k_limit2_euler_quad<3><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq);
+    if (N == 1) k2::k_limit2_euler_quad<1><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq, a.bcd);
+    else if (N == 2) k2::k_limit2_euler_quad<2><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq, a.bcd);
+    else k2::k_limit2_euler_quad<3><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt, lim, a.cap, a.gam, a.lq, a.bcd);
     return;
   }
   DG_DISPATCH2(pde, N, (k2::k_limit2<P_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.inst, a.ctot, a.bc, lc, li, cnt,

@@ -18,7 +18,63 @@ struct LaunchArgs {
   int bc;
   double gam;
   unsigned int* lq;  // work counter of the 2D Euler limiter (zeroed by its launcher), or null
+  const double* bcd;  // boundary data of kBcDmr meshes (see dmr_ghost), or null
 };
+
+// ----------------------------------------------------------------------------- boundaries
+// Boundary condition codes: 0 periodic, 1 outflow (mirror ghosts), 2 the double Mach
+// reflection problem (Example 11, after Woodward and Colella; 2D Euler).
+constexpr int kBcDmr = 2;
+// Layout of the kBcDmr boundary data: post-shock and pre-shock conserved states, the shock
+// line x_s(y, t) = a + b y + c t, then per instance the time of the current state, the
+// top side's y and the time of u^n.
+constexpr int kDmrPost = 0, kDmrPre = 4, kDmrA = 8, kDmrB = 9, kDmrC = 10, kDmrInst = 11, kDmrStride = 3;
+__device__ __forceinline__ double dmr_time(const double* __restrict__ bcd, int inst, int which) {
+  return bcd[kDmrInst + kDmrStride * inst + which];  // 0: current state, 2: u^n
+}
+
+// The ghost cell (ix, iy) outside instance `inst` of a kBcDmr mesh, decided by its centre
+// at the time t of the state it borders: on the left the post-shock state (inflow); on the
+// right the mirror image of the boundary cell (outflow); below, the post-shock state where
+// the centre lies left of a, else a reflecting wall (mirror image, rho v negated); above,
+// the post-shock state left of the shock's position on the top side, x_s(y_top, t), else
+// the pre-shock state.  The x side decides first.  Returns the constant state's conserved
+// variables (c != null), or the interior cell to mirror and its flips.
+struct Ghost {
+  const double* c;   // constant ghost: conserved state, else null
+  int jx, jy;        // interior cell of a mirrored ghost
+  bool fx, fy, fv;   // odd modes in x / in y negated; rho v negated (wall)
+};
+__device__ __forceinline__ Ghost dmr_ghost(const Inst& I, int inst, int ix, int iy, const double* __restrict__ bcd,
+                                           double t) {
+  Ghost gh{nullptr, ix, iy, false, false, false};
+  const double xc = __dadd_rn(I.xL, __dmul_rn((double)ix + 0.5, I.hx));
+  if (ix < 0) {
+    gh.c = bcd + kDmrPost;
+    return gh;
+  }
+  if (iy >= I.ny) {
+    const double ytop = bcd[kDmrInst + kDmrStride * inst + 1];
+    const double xs = __dadd_rn(__dadd_rn(bcd[kDmrA], __dmul_rn(bcd[kDmrB], ytop)), __dmul_rn(bcd[kDmrC], t));
+    gh.c = xc < xs ? bcd + kDmrPost : bcd + kDmrPre;
+    return gh;
+  }
+  if (iy < 0 && xc < bcd[kDmrA]) {
+    gh.c = bcd + kDmrPost;
+    return gh;
+  }
+  if (ix >= I.nx) {
+    gh.jx = 2 * I.nx - 1 - ix;
+    gh.fx = true;
+  }
+  if (iy < 0) {
+    gh.jy = -1 - iy;
+    gh.fy = gh.fv = true;
+  }
+  gh.jx = gh.jx < 0 ? 0 : (gh.jx >= I.nx ? I.nx - 1 : gh.jx);
+  gh.jy = gh.jy < 0 ? 0 : (gh.jy >= I.ny ? I.ny - 1 : gh.jy);
+  return gh;
+}
 
 // Inference weights of the learned indicator (device pointers): W1 BF16 [32][FP] (rows
 // padded with zeros to FP columns), b1 FP32 [32], W2 BF16 [32][32], b2, w3 FP32 [32], b3.
