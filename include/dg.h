@@ -156,8 +156,9 @@ dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int64_t* n_flag
  * point values reconstructed on the subcells of its immediate neighbours (characteristic
  * fields for Euler; dimension by dimension in 2D).  Jacobi update: every troubled cell
  * reads the unlimited neighbours.  In 2D the reciprocals in the nonlinear weights
- * (Eq. (14)) are the hardware's approximations refined to within 1-2 ulp.  Errors:
- * DG_ESTATE if no flags exist for this state. */
+ * (Eq. (14)) are the hardware's approximations refined to within 1-2 ulp.  After the
+ * learned indicator's flags (Euler) the positivity fallback of dg_set_indicator_mlp applies
+ * as in dg_step.  Errors: DG_ESTATE if no flags exist for this state. */
 dg_status dg_cswenolimit(dg_mesh* m);
 
 /* The parent WENO limiter (Qiu and Shu, ref. [qs1]; the limiter Sec. 4 compares CSWENO
@@ -300,10 +301,10 @@ dg_status dg_mlp_predict(dg_mlp* n, const float* X, int64_t B, float* logits);
 /* Attach the network's current weights to the mesh as DG_IND_MLP with threshold tau.
  * DG_IND_MLP flags a cell when the TVB indicator flags it and the network's logit exceeds
  * tau (the network filters the TVB list).  In dg_step (Euler), the plain TVB indicator is
- * the fallback, cell by cell: a TVB-flagged cell the network skipped whose unlimited stage
- * has a non-positive density or pressure at a volume or face Gauss point (FP32 screen,
- * p > 1e-6 |E| required) is limited as the plain method limits it, before the limiter
- * runs; the skipped cells left unlimited therefore pass the screen. */
+ * the positivity fallback, per instance: when a TVB-flagged cell the network skipped has a
+ * non-positive density or pressure at a volume or face Gauss point of its unlimited stage
+ * (FP32 screen, p > 1e-6 |E| required), the instance's stage is redone with all its TVB
+ * flags from the unlimited stage -- the plain method's stage. */
 dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau);
 
 /* Evaluates the network on every cell of the current state and writes the logits to the
@@ -319,15 +320,15 @@ dg_status dg_indicator_logits(dg_mesh* m, float* logits);
 dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* change);
 
 /* Running totals over the limiter passes of dg_step (three per step): cells the TVB
- * indicator flagged, cells actually limited (equal for DG_IND_TVB; the learned subset for
- * DG_IND_MLP) and the number of passes.  reset != 0 zeroes them.  Synchronises the stream. */
+ * indicator flagged, cells passed to the limiter (equal for DG_IND_TVB; for DG_IND_MLP the
+ * learned subset plus the TVB-flagged cells of the instance stages the positivity fallback
+ * redid) and the number of passes.  reset != 0 zeroes them.  Synchronises the stream. */
 dg_status dg_flag_statistics(dg_mesh* m, int64_t* tvb_flagged, int64_t* limited, int64_t* passes, int reset);
 
 /* Positivity fallbacks of the learned indicator since the network was attached: instance
- * stages in which the screen handed skipped cells back to the TVB flags, and instance
- * stages in which a limited cell still fails the screen (as it would in the plain
- * method; counted only while the positivity-preserving scaling is off, since with it on
- * the scaling that follows the limiter restores the check points).  Returns
+ * stages redone with the TVB flags, and redone instance stages in which a limited cell
+ * still fails the screen (counted only while the positivity-preserving scaling is off: with
+ * it on, the scaling that follows the limiter restores the check points instead).  Returns
  * DG_EPOSITIVITY when failures > 0.  Synchronises the stream. */
 dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures);
 

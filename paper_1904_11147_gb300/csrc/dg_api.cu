@@ -66,9 +66,13 @@ void launch_mlp_filter(int dim, int pde, int N, const LaunchArgs& a, double c0, 
                        int* lb_i, int nblocks);
 void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
                             const int* lc, const int* li, const Counters* cnt, unsigned int* fail, int nblocks);
-void launch_positivity_gate(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
-                            const int* la_c, const int* la_i, const Counters* cnt_a, unsigned char* flags,
-                            Counters* cnt_b, int* lb_c, int* lb_i, unsigned int* fail, int nblocks);
+void launch_positivity_skipped(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1,
+                               double gam, const int* la_c, const int* la_i, const Counters* cnt_a,
+                               const unsigned char* flags, unsigned int* fail, int nblocks);
+void launch_scatter_unless(int dim, int pde, int N, const LaunchArgs& a, const double* lim, const int* lc,
+                           const int* li, const Counters* cnt, const unsigned int* skip, int nblocks);
+void launch_filter_inst(cudaStream_t st, const int* la_c, const int* la_i, const Counters* cnt_a,
+                        const unsigned int* mark, Counters* cnt_c, int* lc_c, int* lc_i, int nblocks);
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total);
 cudaError_t upload_tables_parent(const dgt::Tabs* tabs);
 void launch_parent(int dim, int pde, int N, const LaunchArgs& a, const int* lc, const int* li, const Counters* cnt,
@@ -186,10 +190,10 @@ struct dg_mesh {
   void* mlp_buf = nullptr;
   MlpInfer mlp{};
   bool has_mlp = false;
-  int *lb_cell = nullptr, *lb_inst = nullptr;
-  Counters* cnt_b = nullptr;
-  unsigned int* fail = nullptr;              // [2][n_inst]: the gate, then the limited cells
-  unsigned long long* pos_counts = nullptr;  // [0] fallbacks (gate), [1] failures after limiting
+  int *lb_cell = nullptr, *lb_inst = nullptr, *lc_cell = nullptr, *lc_inst = nullptr;
+  Counters *cnt_b = nullptr, *cnt_c = nullptr;
+  unsigned int* fail = nullptr;              // [2][n_inst]: the screen of skipped cells, the final one
+  unsigned long long* pos_counts = nullptr;  // [0] stages redone with the TVB flags, [1] failures after it
   bool use_b = false;                        // dg_cswenolimit limits list B (learned) or A (TVB)
   unsigned long long* flag_totals = nullptr;  // TVB-flagged, limited, passes (dg_step)
   double psi_q[16], psi_p1[4];
@@ -242,8 +246,8 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->flag_totals);
   cudaFree(m->mlp_buf);
   cudaFree(m->d_bcd);
-  cudaFree(m->lb_cell); cudaFree(m->lb_inst);
-  cudaFree(m->cnt_b); cudaFree(m->fail); cudaFree(m->pos_counts);
+  cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
+  cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->fail); cudaFree(m->pos_counts);
   cudaFree(m->pp_counts);
   cudaFree(m->d_kx_hpow);
   delete m;
@@ -594,33 +598,40 @@ static cudaError_t learned_flags(dg_mesh* m, double M) {
   return cudaSuccess;
 }
 
-// limiter on list B with the positivity gate of the learned indicator (Euler).  The only
-// cells where the learned stage can differ from the plain method's are the TVB-flagged
-// cells the network skipped, which stay unlimited; the gate screens them and adds every
-// one whose unlimited state has a non-positive density or pressure at a volume or face
-// Gauss point to list B, so that it is limited as the plain method limits it (Jacobi:
-// the limited value of a cell depends only on the unlimited stage).  List B is then
-// limited; without the positivity-preserving scaling, a screen of its limited cells counts
-// the instances where the plain limiting itself leaves a non-positive point (with the
-// scaling on, the scaling that follows restores the check points instead).
+// limiter on list B with the positivity fallback of the learned indicator (Euler).  The
+// learned stage differs from the plain method's only in the TVB-flagged cells the network
+// skipped, which stay unlimited; they are screened on their unlimited state (density and
+// pressure at the volume and face Gauss points).  An instance where one fails is redone with
+// the plain TVB flags (list C: all its TVB-flagged cells, limited from the unlimited stage,
+// which list B's limited values have not yet overwritten) -- the stage the plain method
+// produces; the other instances get list B's values.  Without the positivity-preserving
+// scaling a final screen of list C counts the instances where even the plain stage fails
+// (with the scaling on, the scaling that follows restores the check points instead).
 static cudaError_t learned_limit(dg_mesh* m) {
   LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
   if (m->pde != DG_EULER) {
     k_limit_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
     return cudaSuccess;
   }
-  unsigned int* fail2 = m->fail + m->n_inst;
+  unsigned int* redo = m->fail;
+  unsigned int* fail3 = m->fail + m->n_inst;
   cudaError_t e = cudaMemsetAsync(m->fail, 0, 2 * sizeof(unsigned int) * m->n_inst, m->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->cnt_c, 0, sizeof(Counters), m->st);
   if (e != cudaSuccess) return e;
-  launch_positivity_gate(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->list_cell, m->list_inst, m->cnt,
-                         m->flags, m->cnt_b, m->lb_cell, m->lb_inst, m->fail, m->limit_blocks);
-  launch_count_fail(m->st, m->fail, m->n_inst, m->pos_counts);
-  k_limit_list(m, m->lb_cell, m->lb_inst, m->cnt_b);
-  m->launches += 2;
+  if (m->dim == 1) launch_limit1(m->pde, m->N, a, m->lb_cell, m->lb_inst, m->cnt_b, m->lim, m->limit_blocks);
+  else launch_limit2(m->pde, m->N, a, m->lb_cell, m->lb_inst, m->cnt_b, m->lim, m->limit_blocks);
+  launch_positivity_skipped(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->list_cell, m->list_inst, m->cnt,
+                            m->flags, redo, m->limit_blocks);
+  launch_count_fail(m->st, redo, m->n_inst, m->pos_counts);
+  launch_scatter_unless(m->dim, m->pde, m->N, a, m->lim, m->lb_cell, m->lb_inst, m->cnt_b, redo, m->limit_blocks);
+  launch_filter_inst(m->st, m->list_cell, m->list_inst, m->cnt, redo, m->cnt_c, m->lc_cell, m->lc_inst,
+                     m->limit_blocks);
+  k_limit_list(m, m->lc_cell, m->lc_inst, m->cnt_c);
+  m->launches += 6;
   if (!m->pp_on) {
-    launch_positivity_list(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->lb_cell, m->lb_inst, m->cnt_b, fail2,
+    launch_positivity_list(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->lc_cell, m->lc_inst, m->cnt_c, fail3,
                            m->limit_blocks);
-    launch_count_fail(m->st, fail2, m->n_inst, m->pos_counts + 1);
+    launch_count_fail(m->st, fail3, m->n_inst, m->pos_counts + 1);
     m->launches += 2;
   }
   return cudaSuccess;
@@ -852,7 +863,8 @@ extern "C" dg_status dg_flag_cells(dg_mesh* m, int indicator, double tvb_M, int6
 extern "C" dg_status dg_cswenolimit(dg_mesh* m) {
   if (!m) return fail(DG_EINVAL, "null mesh");
   if (!m->flags_valid) return fail(DG_ESTATE, "no troubled-cell flags for the current state");
-  k_limit(m);
+  if (m->use_b) CK(learned_limit(m));  // the learned flags, with their positivity fallback
+  else k_limit(m);
   CK(cudaGetLastError());
   m->flags_valid = false;
   return DG_OK;
@@ -947,7 +959,7 @@ static dg_status enqueue_step(dg_mesh* m, int indicator, double M) {
     if (indicator == DG_IND_MLP) {
       CK(learned_flags(m, M));
       CK(learned_limit(m));
-      k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt_b, nullptr, m->flag_totals);
+      k_accum_flags<<<1, 32, 0, m->st>>>(m->cnt, m->cnt_b, m->pde == DG_EULER ? m->cnt_c : nullptr, m->flag_totals);
     } else {
       CK(cudaMemsetAsync(m->cnt, 0, sizeof(Counters), m->st));
       if (indicator == DG_IND_KXRCF) k_flag_kx(m);
@@ -1368,7 +1380,10 @@ extern "C" dg_status dg_set_indicator_mlp(dg_mesh* m, const dg_mlp* n, float tau
     bool ok = cudaMalloc(&m->mlp_buf, infer_bytes(n->FP)) == cudaSuccess &&
               cudaMalloc(&m->lb_cell, sizeof(int) * m->ctot) == cudaSuccess &&
               cudaMalloc(&m->lb_inst, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->lc_cell, sizeof(int) * m->ctot) == cudaSuccess &&
+              cudaMalloc(&m->lc_inst, sizeof(int) * m->ctot) == cudaSuccess &&
               cudaMalloc(&m->cnt_b, sizeof(Counters)) == cudaSuccess &&
+              cudaMalloc(&m->cnt_c, sizeof(Counters)) == cudaSuccess &&
               cudaMalloc(&m->fail, 2 * sizeof(unsigned int) * m->n_inst) == cudaSuccess &&
               cudaMalloc(&m->pos_counts, 2 * sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {

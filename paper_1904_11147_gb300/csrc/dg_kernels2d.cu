@@ -1055,26 +1055,19 @@ __global__ void __launch_bounds__(256)
     const bool inW = lane > 0, inE = lane < TX - 1 && ix + 1 < I.nx;
     const bool inS = w > 0, inN = w < TY - 1 && iy + 1 < I.ny;
     // kBcDmr: the neighbours' U_00 (W, E, S, N) follow dmr_ghost where they lie outside
-    Ghost gh[4];
+    // (decided again per variable: only boundary cells of such meshes take this path)
     const bool dmr = bc == kBcDmr && (ix == 0 || iy == 0 || ix == I.nx - 1 || iy == I.ny - 1);
-    if (dmr) {
-      const int ox[4] = {-1, 1, 0, 0}, oy[4] = {0, 0, -1, 1};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int jx = ix + ox[k], jy = iy + oy[k];
-        const bool out = jx < 0 || jx >= I.nx || jy < 0 || jy >= I.ny;
-        gh[k] = out ? dmr_ghost(I, tile.inst, jx, jy, bcd, dmr_time(bcd, tile.inst, 0))
-                    : Ghost{nullptr, jx, jy, false, false, false};
-      }
-    }
     auto nb_u00 = [&](int k, const double* P, long long gk, int v) -> double {
       if (!dmr) return __ldg(P + gk);
-      if (gh[k].c) return 2.0 * gh[k].c[v];
-      return neg_if(__ldg(P + I.off + (long long)gh[k].jy * I.nx + gh[k].jx), gh[k].fv && v == 2);
+      const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0)), jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+      if (jx >= 0 && jx < I.nx && jy >= 0 && jy < I.ny) return __ldg(P + gk);
+      const Ghost gh = dmr_ghost(I, tile.inst, jx, jy, bcd, dmr_time(bcd, tile.inst, 0));
+      if (gh.c) return 2.0 * gh.c[v];
+      return neg_if(__ldg(P + I.off + (long long)gh.jy * I.nx + gh.jx), gh.fv && v == 2);
     };
     const long long mx2 = __double_as_longlong(M * I.hx * I.hx), my2 = __double_as_longlong(M * I.hy * I.hy);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
+#pragma unroll 1
+    for (int v = 0; v < V; ++v) {  // one variable at a time keeps the kernel at 4 blocks per SM
       const double* P = U + (long long)(v * NP) * ctot;
       const double mean = s_mean[v][w][lane];
       const double mW = inW ? s_mean[v][w][lane - 1] : __dmul_rn(nb_u00(0, P, gW, v), c00);

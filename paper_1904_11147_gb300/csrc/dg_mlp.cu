@@ -18,6 +18,11 @@
 namespace dg {
 
 constexpr int kHid = 32;
+// Row strides (BF16 elements) of the per-warp feature block [32][FP] and of the hidden layer
+// [32][32] in shared memory: 8 elements of padding put the eight rows an mma fragment load
+// reads (and the 32 rows the feature writes touch) on different banks.
+constexpr int kPadX = 8;
+constexpr int kLdH = kHid + 8;
 
 template <int DIM, int PDE, int N>
 struct FeatDims {
@@ -119,16 +124,14 @@ __device__ __forceinline__ void cell_features(const double* __restrict__ U, long
   int k = 0;
 #pragma unroll 1
   for (int v = 0; v < V; ++v) {
-    double own[NP], nb[NB][NP];
+    double own[NP];
     load_var<DIM, NP>(U, ctot, cr[0], v, own);
-#pragma unroll
-    for (int c = 0; c < NB; ++c) load_var<DIM, NP>(U, ctot, cr[c + 1], v, nb[c]);
     const double mj = own[0] * c0;
     float d[NB];
     float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) {
-      d[c] = d2f_trunc(nb[c][0] * c0 - mj);
+    for (int c = 0; c < NB; ++c) {  // neighbour means first (U_0 has no mirror sign)
+      d[c] = d2f_trunc(__ldg(U + (long long)(v * NP) * ctot + cr[c + 1].g) * c0 - mj);
       s = fmaxf(s, fabsf(d[c]));
     }
 #pragma unroll
@@ -138,10 +141,14 @@ __device__ __forceinline__ void cell_features(const double* __restrict__ U, long
     for (int c = 0; c < NB; ++c) put(k++, d[c] * inv);
 #pragma unroll
     for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(own[m]) * inv);
+    // then one neighbour's higher modes at a time (few registers live)
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
+    for (int c = 0; c < NB; ++c) {
+      double nb[NP];
+      load_var<DIM, NP>(U, ctot, cr[c + 1], v, nb);
 #pragma unroll
-      for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(nb[c][m]) * inv);
+      for (int m = 1; m < NP; ++m) put(k++, d2f_trunc(nb[m]) * inv);
+    }
   }
 }
 
@@ -182,9 +189,10 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
 __device__ __forceinline__ unsigned ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const unsigned*>(p); }
 
 // The 32-32-1 network on the 32 cells of a warp.  Xs: this warp's [32][FP] BF16 features
-// (reused for the hidden layer); returns the logit of the lane's cell.
+// with row stride FP + kPadX (reused for the hidden layer); returns the logit of the lane's cell.
 __device__ __forceinline__ float warp_mlp(__nv_bfloat16* Xs, int FP, const MlpInfer& W) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int LX = FP + kPadX;
   float acc[2][4][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
@@ -197,8 +205,8 @@ __device__ __forceinline__ float warp_mlp(__nv_bfloat16* Xs, int FP, const MlpIn
     unsigned a[2][4], b[4][2];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-      const __nv_bfloat16* r0 = Xs + (mt * 16 + g) * FP + k0 + 2 * t;
-      const __nv_bfloat16* r1 = r0 + 8 * FP;
+      const __nv_bfloat16* r0 = Xs + (mt * 16 + g) * LX + k0 + 2 * t;
+      const __nv_bfloat16* r1 = r0 + 8 * LX;
       a[mt][0] = ld_pair(r0);
       a[mt][1] = ld_pair(r1);
       a[mt][2] = ld_pair(r0 + 8);
@@ -224,10 +232,10 @@ __device__ __forceinline__ float warp_mlp(__nv_bfloat16* Xs, int FP, const MlpIn
     for (int nt = 0; nt < 4; ++nt) {
       const int col = nt * 8 + 2 * t;
       const float bb0 = __ldg(W.b1 + col), bb1 = __ldg(W.b1 + col + 1);
-      Hs[(mt * 16 + g) * kHid + col] = __float2bfloat16_rn(fmaxf(acc[mt][nt][0] + bb0, 0.f));
-      Hs[(mt * 16 + g) * kHid + col + 1] = __float2bfloat16_rn(fmaxf(acc[mt][nt][1] + bb1, 0.f));
-      Hs[(mt * 16 + g + 8) * kHid + col] = __float2bfloat16_rn(fmaxf(acc[mt][nt][2] + bb0, 0.f));
-      Hs[(mt * 16 + g + 8) * kHid + col + 1] = __float2bfloat16_rn(fmaxf(acc[mt][nt][3] + bb1, 0.f));
+      Hs[(mt * 16 + g) * kLdH + col] = __float2bfloat16_rn(fmaxf(acc[mt][nt][0] + bb0, 0.f));
+      Hs[(mt * 16 + g) * kLdH + col + 1] = __float2bfloat16_rn(fmaxf(acc[mt][nt][1] + bb1, 0.f));
+      Hs[(mt * 16 + g + 8) * kLdH + col] = __float2bfloat16_rn(fmaxf(acc[mt][nt][2] + bb0, 0.f));
+      Hs[(mt * 16 + g + 8) * kLdH + col + 1] = __float2bfloat16_rn(fmaxf(acc[mt][nt][3] + bb1, 0.f));
       acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
     }
   __syncwarp();
@@ -236,8 +244,8 @@ __device__ __forceinline__ float warp_mlp(__nv_bfloat16* Xs, int FP, const MlpIn
     unsigned a[2][4], b[4][2];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-      const __nv_bfloat16* r0 = Hs + (mt * 16 + g) * kHid + k0 + 2 * t;
-      const __nv_bfloat16* r1 = r0 + 8 * kHid;
+      const __nv_bfloat16* r0 = Hs + (mt * 16 + g) * kLdH + k0 + 2 * t;
+      const __nv_bfloat16* r1 = r0 + 8 * kLdH;
       a[mt][0] = ld_pair(r0);
       a[mt][1] = ld_pair(r1);
       a[mt][2] = ld_pair(r0 + 8);
@@ -301,13 +309,13 @@ __global__ void __launch_bounds__(256)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int FP = W.FP;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem_raw) + w * 32 * FP;
+  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem_raw) + w * 32 * (FP + kPadX);
   const Tile t = tiles[blockIdx.x];
   const Inst I = insts[t.inst];
   int ix, iy;
   tile_cell<DIM>(t, ix, iy);
   const bool active = ix < I.nx && iy < I.ny;
-  __nv_bfloat16* row = Xs + lane * FP;
+  __nv_bfloat16* row = Xs + lane * (FP + kPadX);
   using D = FeatDims<DIM, PDE, N>;
   if (active) {
     cell_features<DIM, PDE, N>(U, ctot, I, ix, iy, bc, c0, [&](int k, float v) { row[k] = __float2bfloat16_rn(v); });
@@ -333,9 +341,10 @@ __global__ void __launch_bounds__(256)
 // tau: every warp takes 32 consecutive entries of the TVB list (A), computes their
 // features, runs the network on the tensor cores and appends the kept cells to list B
 // (warp ballot + one atomic per warp).  flags[] receives the final decision in bit 0 and
-// keeps the TVB pass's near-threshold bit 1.
+// keeps the TVB pass's near-threshold bit 1.  Three blocks per SM (80 registers): the kernel is
+// latency-bound (gathered loads, shared memory), so more resident warps hide more of it.
 template <int DIM, int PDE, int N>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_mlp_filter(const double* __restrict__ U, const Inst* __restrict__ insts, long long ctot, int bc, double c0,
                  MlpInfer W, const int* __restrict__ la_cell, const int* __restrict__ la_inst,
                  const Counters* __restrict__ cnt_a, unsigned char* __restrict__ flags, Counters* cnt_b,
@@ -344,8 +353,8 @@ __global__ void __launch_bounds__(256, 2)
   using D = FeatDims<DIM, PDE, N>;
   const int FP = W.FP;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem_raw) + w * 32 * FP;
-  __nv_bfloat16* row = Xs + lane * FP;
+  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem_raw) + w * 32 * (FP + kPadX);
+  __nv_bfloat16* row = Xs + lane * (FP + kPadX);
   const unsigned int n = cnt_a->n_flag;
   const unsigned int warps_total = gridDim.x * (blockDim.x >> 5);
   for (unsigned int base = (blockIdx.x * (blockDim.x >> 5) + w) * 32u; base < n; base += warps_total * 32u) {
@@ -465,41 +474,57 @@ __global__ void __launch_bounds__(128) k_positivity_list(const double* __restric
   }
 }
 
-// Positivity gate of the learned indicator: every TVB-listed cell the network skipped
-// (bit 0 of flags[g] clear) whose unlimited state fails the screen is added to the kept
-// list B (warp ballot, one atomic per warp) and to the flags, so that it is limited as
-// the plain method limits it; its instance is marked in fail[] (counted as a fallback).
+// Positivity screen of the cells the learned indicator skipped: every cell of list A (the
+// TVB list) with bit 0 of flags[g] clear whose unlimited state fails the screen marks its
+// instance in fail[].
 template <int DIM, int N>
-__global__ void __launch_bounds__(128) k_positivity_gate(const double* __restrict__ U, long long ctot,
-                                                         const int* __restrict__ la_cell,
-                                                         const int* __restrict__ la_inst,
-                                                         const Counters* __restrict__ cnt_a,
-                                                         unsigned char* __restrict__ flags, PosTab tb,
-                                                         Counters* cnt_b, int* __restrict__ lb_cell,
-                                                         int* __restrict__ lb_inst, unsigned int* __restrict__ fail) {
+__global__ void __launch_bounds__(128) k_positivity_skipped(const double* __restrict__ U, long long ctot,
+                                                            const int* __restrict__ la_cell,
+                                                            const int* __restrict__ la_inst,
+                                                            const Counters* __restrict__ cnt_a,
+                                                            const unsigned char* __restrict__ flags, PosTab tb,
+                                                            unsigned int* __restrict__ fail) {
+  const unsigned int n = cnt_a->n_flag;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long g = la_cell[i];
+    if (!(flags[g] & 1) && screen_fails<DIM, N>(U, ctot, g, tb)) atomicOr(fail + la_inst[i], 1u);
+  }
+}
+
+// Writes the limited modes 1..NP-1 of the listed cells whose instance is not marked in skip[].
+template <int V, int NP>
+__global__ void k_scatter_unless(double* __restrict__ Ust, long long ctot, const double* __restrict__ lim,
+                                 long long cap, const int* __restrict__ list_cell, const int* __restrict__ list_inst,
+                                 const Counters* __restrict__ cnt, const unsigned int* __restrict__ skip) {
+  const unsigned int n = cnt->n_flag;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (skip[list_inst[i]]) continue;
+    const long long g = list_cell[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int m = 1; m < NP; ++m) Ust[(long long)(v * NP + m) * ctot + g] = lim[(long long)(v * NP + m) * cap + i];
+  }
+}
+
+// List C = the entries of list A that belong to marked instances.
+__global__ void k_filter_inst(const int* __restrict__ la_cell, const int* __restrict__ la_inst,
+                              const Counters* __restrict__ cnt_a, const unsigned int* __restrict__ mark, Counters* cnt_c,
+                              int* __restrict__ lc_cell, int* __restrict__ lc_inst) {
   const unsigned int n = cnt_a->n_flag;
   const int lane = threadIdx.x & 31;
   const unsigned int stride = gridDim.x * blockDim.x;
   for (unsigned int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
     const unsigned int i = base + lane;
-    bool add = false;
-    long long g = 0;
-    int ii = 0;
-    if (i < n) {
-      g = la_cell[i];
-      ii = la_inst[i];
-      add = !(flags[g] & 1) && screen_fails<DIM, N>(U, ctot, g, tb);
-    }
-    const unsigned int bal = __ballot_sync(0xffffffffu, add);
+    const bool keep = i < n && mark[la_inst[i]];
+    const unsigned int bal = __ballot_sync(0xffffffffu, keep);
     unsigned int pos0 = 0;
-    if (lane == 0 && bal) pos0 = atomicAdd(&cnt_b->n_flag, (unsigned)__popc(bal));
+    if (lane == 0 && bal) pos0 = atomicAdd(&cnt_c->n_flag, (unsigned)__popc(bal));
     pos0 = __shfl_sync(0xffffffffu, pos0, 0);
-    if (add) {
+    if (keep) {
       const unsigned int p = pos0 + __popc(bal & ((1u << lane) - 1u));
-      lb_cell[p] = (int)g;
-      lb_inst[p] = ii;
-      flags[g] |= 1;
-      atomicOr(fail + ii, 1u);
+      lc_cell[p] = la_cell[i];
+      lc_inst[p] = la_inst[i];
     }
   }
 }
@@ -750,7 +775,7 @@ void launch_features(int dim, int pde, int N, const LaunchArgs& a, double c0, fl
                                                                                     c0, X)));
 }
 
-size_t flag_mlp_smem(int FP) { return sizeof(__nv_bfloat16) * 256 * (size_t)FP; }
+size_t flag_mlp_smem(int FP) { return sizeof(__nv_bfloat16) * 256 * (size_t)(FP + kPadX); }
 
 cudaError_t prepare_mlp(int dim, int pde, int N, int FP) {
   cudaError_t e = cudaSuccess;
@@ -810,12 +835,23 @@ void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* p
   DG_POS_DISPATCH(dim, N, (k_positivity_list<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, lc, li, cnt, tb, fail)));
 }
 
-void launch_positivity_gate(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
-                            const int* la_c, const int* la_i, const Counters* cnt_a, unsigned char* flags,
-                            Counters* cnt_b, int* lb_c, int* lb_i, unsigned int* fail, int nblocks) {
+void launch_positivity_skipped(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1,
+                               double gam, const int* la_c, const int* la_i, const Counters* cnt_a,
+                               const unsigned char* flags, unsigned int* fail, int nblocks) {
   const PosTab tb = pos_tab(N, psi_q, psi_p1, gam);
-  DG_POS_DISPATCH(dim, N, (k_positivity_gate<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, la_c, la_i, cnt_a, flags,
-                                                                                  tb, cnt_b, lb_c, lb_i, fail)));
+  DG_POS_DISPATCH(dim, N, (k_positivity_skipped<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, la_c, la_i, cnt_a,
+                                                                                      flags, tb, fail)));
+}
+
+void launch_scatter_unless(int dim, int pde, int N, const LaunchArgs& a, const double* lim, const int* lc,
+                           const int* li, const Counters* cnt, const unsigned int* skip, int nblocks) {
+  DG_DISPATCH_ALL(dim, pde, N, (k_scatter_unless<nv_of(D_, P_), np_of(D_, N_)><<<nblocks, 256, 0, a.st>>>(
+                                   a.out, a.ctot, lim, a.cap, lc, li, cnt, skip)));
+}
+
+void launch_filter_inst(cudaStream_t st, const int* la_c, const int* la_i, const Counters* cnt_a,
+                        const unsigned int* mark, Counters* cnt_c, int* lc_c, int* lc_i, int nblocks) {
+  k_filter_inst<<<nblocks, 256, 0, st>>>(la_c, la_i, cnt_a, mark, cnt_c, lc_c, lc_i);
 }
 
 void launch_count_fail(cudaStream_t st, const unsigned int* fail, int n_inst, unsigned long long* total) {
