@@ -326,9 +326,11 @@ dg_status dg_harvest(dg_mesh* m, double tvb_M, float* X, uint8_t* flags, float* 
 dg_status dg_flag_statistics(dg_mesh* m, int64_t* tvb_flagged, int64_t* limited, int64_t* passes, int reset);
 
 /* Positivity fallbacks of the learned indicator since the network was attached: instance
- * stages redone with the TVB flags, and redone instance stages in which a limited cell
- * still fails the screen (counted only while the positivity-preserving scaling is off: with
- * it on, the scaling that follows the limiter restores the check points instead).  Returns
+ * stages redone with the TVB flags, and instance stages whose final state still fails the
+ * screen at some cell (every cell is screened; counted only while the positivity-preserving
+ * scaling is off: with it on, the scaling that follows the limiter restores the check points
+ * instead).  A failure outside the cells the network skipped is one the plain method's
+ * stage from the same input has as well.  Returns
  * DG_EPOSITIVITY when failures > 0.  Synchronises the stream. */
 dg_status dg_positivity_report(dg_mesh* m, int64_t* fallbacks, int64_t* failures);
 

@@ -49,8 +49,9 @@ void launch_label(int dim, int pde, int N, const LaunchArgs& a, double c0, const
                   const Counters* cnt, const double* lim, float* label, int nblocks);
 void launch_mlp_fb(cudaStream_t st, const float* X, const unsigned char* y, long long B, int F, const float* params,
                    float pw, float* h1, float* d1, float* h2, float* d2, float* dz, float* loss);
+long long mlp_wgrad_chunks(long long B);
 void launch_mlp_wgrad(cudaStream_t st, const float* X, long long B, int F, const float* h1, const float* d1,
-                      const float* h2, const float* d2, const float* dz, float* grad);
+                      const float* h2, const float* d2, const float* dz, float* part, float* grad);
 void launch_mlp_forward(cudaStream_t st, const float* X, long long B, int F, const float* params, float* z);
 void launch_mlp_adam(cudaStream_t st, float* params, const float* grad, float* m1, float* m2, int P, float lr, int t);
 void launch_mlp_export(cudaStream_t st, const float* params, int F, int FP, void* W1b, float* b1, void* W2b, float* b2,
@@ -64,8 +65,8 @@ cudaError_t prepare_filter(int dim, int pde, int N, int FP);
 void launch_mlp_filter(int dim, int pde, int N, const LaunchArgs& a, double c0, const MlpInfer& W, const int* la_c,
                        const int* la_i, const Counters* cnt_a, unsigned char* flags, Counters* cnt_b, int* lb_c,
                        int* lb_i, int nblocks);
-void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
-                            const int* lc, const int* li, const Counters* cnt, unsigned int* fail, int nblocks);
+void launch_positivity_all(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
+                           const int* cell_inst, unsigned int* fail, int nblocks);
 void launch_positivity_skipped(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1,
                                double gam, const int* la_c, const int* la_i, const Counters* cnt_a,
                                const unsigned char* flags, unsigned int* fail, int nblocks);
@@ -604,9 +605,11 @@ static cudaError_t learned_flags(dg_mesh* m, double M) {
 // pressure at the volume and face Gauss points).  An instance where one fails is redone with
 // the plain TVB flags (list C: all its TVB-flagged cells, limited from the unlimited stage,
 // which list B's limited values have not yet overwritten) -- the stage the plain method
-// produces; the other instances get list B's values.  Without the positivity-preserving
-// scaling a final screen of list C counts the instances where even the plain stage fails
-// (with the scaling on, the scaling that follows restores the check points instead).
+// produces; the other instances get list B's values.  Cells outside the skipped ones
+// (unflagged, or limited on the network's list) take the same values in the plain stage,
+// so a failure there is one the redo cannot change: without the positivity-preserving
+// scaling a final screen of every cell of the stage counts the instances whose stage still
+// fails (with the scaling on, the scaling that follows restores the check points instead).
 static cudaError_t learned_limit(dg_mesh* m) {
   LaunchArgs a = args<LaunchArgs>(m, 0, m->cur, m->cur);
   if (m->pde != DG_EULER) {
@@ -629,8 +632,7 @@ static cudaError_t learned_limit(dg_mesh* m) {
   k_limit_list(m, m->lc_cell, m->lc_inst, m->cnt_c);
   m->launches += 6;
   if (!m->pp_on) {
-    launch_positivity_list(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->lc_cell, m->lc_inst, m->cnt_c, fail3,
-                           m->limit_blocks);
+    launch_positivity_all(m->dim, m->N, a, m->psi_q, m->psi_p1, m->gamma, m->d_cell_inst, fail3, m->sms * 8);
     launch_count_fail(m->st, fail3, m->n_inst, m->pos_counts + 1);
     m->launches += 2;
   }
@@ -1204,6 +1206,7 @@ struct dg_mlp {
   void* infer = nullptr;  // BF16 W1 [32][FP], BF16 W2 [32][32], FP32 b1, b2, w3, b3
   long long cap = 0;
   float *h1 = nullptr, *d1 = nullptr, *h2 = nullptr, *d2 = nullptr, *dz = nullptr;
+  float* part = nullptr;  // per-chunk weight gradients [chunks][P]
 };
 
 static const int kHidden = 32;
@@ -1242,7 +1245,7 @@ extern "C" size_t dg_mlp_param_count(const dg_mlp* n) { return n ? (size_t)n->P 
 extern "C" dg_status dg_mlp_destroy(dg_mlp* n) {
   if (!n) return DG_OK;
   cudaFree(n->params); cudaFree(n->grad); cudaFree(n->m1); cudaFree(n->m2); cudaFree(n->loss); cudaFree(n->infer);
-  cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz);
+  cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz); cudaFree(n->part);
   delete n;
   return DG_OK;
 }
@@ -1317,22 +1320,22 @@ extern "C" dg_status dg_mlp_set_params(dg_mlp* n, const float* in, size_t count)
 
 static dg_status mlp_backward(dg_mlp* n, const float* X, const uint8_t* y, int64_t B, float pw) {
   if (B > n->cap) {
-    cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz);
-    n->h1 = n->d1 = n->h2 = n->d2 = n->dz = nullptr;
+    cudaFree(n->h1); cudaFree(n->d1); cudaFree(n->h2); cudaFree(n->d2); cudaFree(n->dz); cudaFree(n->part);
+    n->h1 = n->d1 = n->h2 = n->d2 = n->dz = n->part = nullptr;
     const size_t hb = sizeof(float) * kHidden * (size_t)B;
     if (cudaMalloc(&n->h1, hb) != cudaSuccess || cudaMalloc(&n->d1, hb) != cudaSuccess ||
         cudaMalloc(&n->h2, hb) != cudaSuccess || cudaMalloc(&n->d2, hb) != cudaSuccess ||
-        cudaMalloc(&n->dz, sizeof(float) * (size_t)B) != cudaSuccess) {
+        cudaMalloc(&n->dz, sizeof(float) * (size_t)B) != cudaSuccess ||
+        cudaMalloc(&n->part, sizeof(float) * (size_t)n->P * (size_t)mlp_wgrad_chunks(B)) != cudaSuccess) {
       cudaGetLastError();
       n->cap = 0;
       return fail(DG_ENOMEM, "training scratch for %lld samples", (long long)B);
     }
     n->cap = B;
   }
-  CK(cudaMemsetAsync(n->grad, 0, sizeof(float) * n->P, n->st));
   CK(cudaMemsetAsync(n->loss, 0, sizeof(float), n->st));
   launch_mlp_fb(n->st, X, y, B, n->F, n->params, pw, n->h1, n->d1, n->h2, n->d2, n->dz, n->loss);
-  launch_mlp_wgrad(n->st, X, B, n->F, n->h1, n->d1, n->h2, n->d2, n->dz, n->grad);
+  launch_mlp_wgrad(n->st, X, B, n->F, n->h1, n->d1, n->h2, n->d2, n->dz, n->part, n->grad);
   CK(cudaGetLastError());
   return DG_OK;
 }

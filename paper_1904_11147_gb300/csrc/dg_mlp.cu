@@ -461,17 +461,13 @@ __device__ __forceinline__ bool screen_fails(const double* __restrict__ U, long 
   return bad;
 }
 
-// Screens the listed cells and marks the instances of failing ones in fail[].
+// Screens every cell of the mesh and marks the instances of failing ones in fail[].
 template <int DIM, int N>
-__global__ void __launch_bounds__(128) k_positivity_list(const double* __restrict__ U, long long ctot,
-                                                         const int* __restrict__ list_cell,
-                                                         const int* __restrict__ list_inst,
-                                                         const Counters* __restrict__ cnt, PosTab tb,
-                                                         unsigned int* __restrict__ fail) {
-  const unsigned int n = cnt->n_flag;
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (screen_fails<DIM, N>(U, ctot, list_cell[i], tb)) atomicOr(fail + list_inst[i], 1u);
-  }
+__global__ void __launch_bounds__(128) k_positivity_all(const double* __restrict__ U, long long ctot, long long ncell,
+                                                        const int* __restrict__ cell_inst, PosTab tb,
+                                                        unsigned int* __restrict__ fail) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ncell; g += (long long)gridDim.x * blockDim.x)
+    if (screen_fails<DIM, N>(U, ctot, g, tb)) atomicOr(fail + cell_inst[g], 1u);
 }
 
 // Positivity screen of the cells the learned indicator skipped: every cell of list A (the
@@ -685,11 +681,13 @@ __global__ void k_mlp_forward(const float* __restrict__ X, long long B, int F, c
   z_out[b] = z;
 }
 
-// Weight gradients over a chunk of samples: grad[p] += sum_b delta[b][o] * input[b][i].
+// Weight gradients over a chunk of samples: part[chunk][p] = sum_b delta[b][o] * input[b][i]
+// over the chunk's samples; k_mlp_wsum adds the chunks in a fixed order, so that training is
+// reproducible bit for bit.
 constexpr int kChunk = 64;
 __global__ void k_mlp_wgrad(const float* __restrict__ X, long long B, int F, const float* __restrict__ h1s,
                             const float* __restrict__ d1s, const float* __restrict__ h2s, const float* __restrict__ d2s,
-                            const float* __restrict__ dzs, float* __restrict__ grad) {
+                            const float* __restrict__ dzs, float* __restrict__ part) {
   const long long b0 = (long long)blockIdx.x * kChunk;
   const int nb = (int)min((long long)kChunk, B - b0);
   const int P = kHid * F + kHid + kHid * kHid + kHid + kHid + 1;
@@ -713,8 +711,16 @@ __global__ void k_mlp_wgrad(const float* __restrict__ X, long long B, int F, con
     } else {  // b3
       for (int j = 0; j < nb; ++j) s += dzs[b0 + j];
     }
-    atomicAdd(grad + p, s);
+    part[(long long)blockIdx.x * P + p] = s;
   }
+}
+
+__global__ void k_mlp_wsum(const float* __restrict__ part, int nchunks, int P, float* __restrict__ grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float s = 0.f;
+  for (int c = 0; c < nchunks; ++c) s += part[(long long)c * P + p];
+  grad[p] = s;
 }
 
 // Adam with bias correction on the FP32 master parameters; refreshes the inference copy
@@ -829,10 +835,11 @@ static PosTab pos_tab(int N, const double* psi_q /* [N+1][N+1] */, const double*
     }                                     \
   } while (0)
 
-void launch_positivity_list(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
-                            const int* lc, const int* li, const Counters* cnt, unsigned int* fail, int nblocks) {
+void launch_positivity_all(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1, double gam,
+                           const int* cell_inst, unsigned int* fail, int nblocks) {
   const PosTab tb = pos_tab(N, psi_q, psi_p1, gam);
-  DG_POS_DISPATCH(dim, N, (k_positivity_list<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, lc, li, cnt, tb, fail)));
+  DG_POS_DISPATCH(dim, N, (k_positivity_all<D_, N_><<<nblocks, 128, 0, a.st>>>(a.us, a.ctot, a.ncell, cell_inst, tb,
+                                                                                  fail)));
 }
 
 void launch_positivity_skipped(int dim, int N, const LaunchArgs& a, const double* psi_q, const double* psi_p1,
@@ -887,9 +894,14 @@ void launch_mlp_forward(cudaStream_t st, const float* X, long long B, int F, con
   k_mlp_forward<<<(unsigned)((B + 127) / 128), 128, smem, st>>>(X, B, F, params, z);
 }
 
+long long mlp_wgrad_chunks(long long B) { return (B + kChunk - 1) / kChunk; }
+
 void launch_mlp_wgrad(cudaStream_t st, const float* X, long long B, int F, const float* h1, const float* d1,
-                      const float* h2, const float* d2, const float* dz, float* grad) {
-  k_mlp_wgrad<<<(unsigned)((B + kChunk - 1) / kChunk), 256, 0, st>>>(X, B, F, h1, d1, h2, d2, dz, grad);
+                      const float* h2, const float* d2, const float* dz, float* part, float* grad) {
+  const long long nc = mlp_wgrad_chunks(B);
+  const int P = kHid * F + kHid + kHid * kHid + kHid + kHid + 1;
+  k_mlp_wgrad<<<(unsigned)nc, 256, 0, st>>>(X, B, F, h1, d1, h2, d2, dz, part);
+  k_mlp_wsum<<<(P + 255) / 256, 256, 0, st>>>(part, (int)nc, P, grad);
 }
 
 void launch_mlp_adam(cudaStream_t st, float* params, const float* grad, float* m1, float* m2, int P, float lr,

@@ -7,8 +7,8 @@ instance's stage is redone with all its TVB flags: the plain method's stage.  He
 network never keeps a cell, so per instance and stage the library must produce the
 unlimited stage, or oracle.limit(stage, flag_tvb(stage)) when a TVB-flagged cell fails the
 screen; its fallback count must equal the number of redone (instance, stage) pairs and its
-failure count the redone ones where a limited cell still fails, both recomputed on the
-host.  The states are chosen so that no screened point lies near the decision (the FP64
+failure count the (instance, stage) pairs whose final stage still fails the screen at some
+cell, both recomputed on the host.  The states are chosen so that no screened point lies near the decision (the FP64
 host recomputation then decides exactly as the FP32 kernel).
 """
 import math
@@ -52,18 +52,18 @@ def _screen_margin(u):
 
 def _oracle_fallback(o, st):
     """The learned stage with a network that keeps no cell, with the positivity fallback:
-    (result, redone, failed)."""
+    (result, redone, failed).  Only the TVB-flagged cells the network skipped can make the
+    plain stage differ, so they decide the redo; the final screen covers every cell."""
     fl, _, _ = o.flag_tvb(st, 0.01)
-    if not fl.any():
-        return st, 0, 0
-    mg = _screen_margin(st)[fl == 1]
-    assert np.abs(mg[np.isfinite(mg)]).min() > 1e-5, "a screened point lies near the decision"
-    if (mg > 0).all():
-        return st, 0, 0
-    res = o.limit(st, fl)
-    mg2 = _screen_margin(res)[fl == 1]
+    res, redo = st, 0
+    if fl.any():
+        mg = _screen_margin(st)[fl == 1]
+        assert np.abs(mg[np.isfinite(mg)]).min() > 1e-5, "a screened point lies near the decision"
+        if not (mg > 0).all():
+            res, redo = o.limit(st, fl), 1
+    mg2 = _screen_margin(res)
     assert np.abs(mg2[np.isfinite(mg2)]).min() > 1e-5
-    return res, 1, int(not (mg2 > 0).all())
+    return res, redo, int(not (mg2 > 0).all())
 
 
 def _oracle_learned_none_step(o, u, dt):
