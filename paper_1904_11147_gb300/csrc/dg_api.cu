@@ -86,7 +86,7 @@ void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long 
                          int nblocks);
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* pg, const double* pl, double c0, double gam, double eps0,
-                       unsigned long long* counts, int nblocks);
+                       int* list, unsigned int* n_list, unsigned long long* counts, int nblocks);
 }  // namespace dg
 
 using namespace dg;
@@ -204,6 +204,8 @@ struct dg_mesh {
   bool pp_on = false;
   double pp_eps0 = 1e-13;
   unsigned long long* pp_counts = nullptr;
+  int* pp_list = nullptr;          // Euler: cells the FP32 screen of the scaling leaves to FP64
+  unsigned int* pp_n = nullptr;
   bool g_pp = false;
   double g_pp_eps = 0.0;
   // KXRCF indicator: r^((N+1)/2) per instance (r the circumscribed radius) and the basis
@@ -249,7 +251,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_bcd);
   cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
   cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->fail); cudaFree(m->pos_counts);
-  cudaFree(m->pp_counts);
+  cudaFree(m->pp_counts); cudaFree(m->pp_list); cudaFree(m->pp_n);
   cudaFree(m->d_kx_hpow);
   delete m;
   return DG_OK;
@@ -392,6 +394,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->d_speed, sizeof(double) * 2 * n_inst) &&
             alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long)) &&
             alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long)) &&
+            (pde != DG_EULER || (alloc((void**)&m->pp_list, sizeof(int) * off) &&
+                                 alloc((void**)&m->pp_n, sizeof(unsigned int)))) &&
             alloc((void**)&m->d_kx_hpow, sizeof(double) * n_inst) &&
             (bc != DG_BC_DMR || alloc((void**)&m->d_bcd, sizeof(double) * (kDmrInst + kDmrStride * n_inst)));
   if (!ok) {
@@ -681,8 +685,8 @@ static void k_pp(dg_mesh* m, double eps0) {
   const long long want = (m->ncell + 127) / 128;
   const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
   launch_positivity(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->pp_g, m->pp_l, mean_factor(m),
-                    m->gamma, eps0, m->pp_counts, nb);
-  m->launches++;
+                    m->gamma, eps0, m->pp_list, m->pp_n, m->pp_counts, nb);
+  m->launches += 2;
 }
 
 // Adds the TVB list length and the limited list length of one pass to running totals

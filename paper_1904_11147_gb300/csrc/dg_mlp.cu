@@ -13,6 +13,7 @@
 
 #include <cuda_bf16.h>
 
+#include "dg_convert.cuh"
 #include "dg_shared.cuh"
 
 namespace dg {
@@ -36,17 +37,6 @@ int mlp_features(int dim, int pde, int N) {
   return V * (NB + (NB + 1) * (NP - 1));
 }
 int mlp_padded(int F) { return (F + 15) / 16 * 16; }
-
-// double -> float by truncation of the significand on the integer pipe (keeps the FP64
-// pipe, the bottleneck of the method on GB300, free); values below the float range give 0.
-__device__ __forceinline__ float d2f_trunc(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
-  return __uint_as_float(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7fffffu));
-}
 
 // Loads the modes of a cell with the boundary condition (periodic wrap; outflow mirror).
 template <int DIM, int V, int NP>

@@ -14,55 +14,66 @@
 //      taken 1e-12 (relative) below the exact root so that rounding cannot leave p below
 //      eps near vacuum; theta2 = min t scales the modes n >= 1 of every variable.
 // A cell whose mean is not admissible is left as it is and counted.
+// Most cells need no scaling: an FP32 evaluation of the check points with error margins
+// (below) proves theta1 = theta2 = 1 for them, and only the others take the FP64 path.
+#include "dg_convert.cuh"
 #include "dg_shared.cuh"
 
 namespace dg {
 
-struct PpTab {
-  double pg[4][4];  // psi_n at the N+1 Gauss points [i][n]
-  double pl[3][4];  // psi_n at the L Gauss-Lobatto points [j][n] (-1, 0, 1; or -1, 1 for N = 1)
-  double c0, gm1, eps0;
+template <typename T>
+struct PpTabT {
+  T pg[4][4];  // psi_n at the N+1 Gauss points [i][n]
+  T pl[3][4];  // psi_n at the L Gauss-Lobatto points [j][n] (-1, 0, 1; or -1, 1 for N = 1)
 };
+struct PpTab : PpTabT<double> {
+  double c0, gm1, eps0;
+  PpTabT<float> f;  // the same tables in FP32 for the screen
+  float p1[4];      // psi_n(1) = max |psi_n| on [-1, 1]
+};
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
 // Calls f(w) with the V point values of the modes u[0..V-1] at every check point: in 1D
 // the Gauss-Lobatto points; in 2D (Gauss x Gauss-Lobatto) then (Gauss-Lobatto x Gauss),
 // by sum factorisation over the Gauss coordinate.  Both point sets are symmetric about 0
 // and psi_n has the parity of n, so even and odd parts are summed once per pair of points
 // (psi_n(0) = 0 for odd n).  The order of the points is not part of the result (minima).
-template <int DIM, int N, int V, class F>
-__device__ __forceinline__ void for_points(const double (*u)[np_of(DIM, N)], const PpTab& tb, F&& f) {
+template <int DIM, int N, int V, typename T, class F>
+__device__ __forceinline__ void for_points(const T (*u)[np_of(DIM, N)], const PpTabT<T>& tb, F&& f) {
   constexpr int L = N == 1 ? 2 : 3, NP = np_of(DIM, N);
   if constexpr (DIM == 1) {
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-      double w[V];
+      T w[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) s = fma(u[v][k], tb.pl[j][k], s);
+        for (int k = 0; k < NP; ++k) s = fma_t(u[v][k], tb.pl[j][k], s);
         w[v] = s;
       }
       f(w);
     }
   } else {
     // values of sum_c t_c psi_c(l) at the Gauss-Lobatto points l = -1, (0,) 1
-    auto lobatto = [&](const double (&t)[V][N + 1]) {
-      double wp[V], wm[V], w0[V];
+    auto lobatto = [&](const T (&t)[V][N + 1]) {
+      T wp[V], wm[V], w0[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        double ev = t[v][0] * tb.pl[L - 1][0], od = t[v][1] * tb.pl[L - 1][1];
+        T ev = t[v][0] * tb.pl[L - 1][0], od = t[v][1] * tb.pl[L - 1][1];
 #pragma unroll
         for (int c = 2; c <= N; ++c) {
-          if (c & 1) od = fma(t[v][c], tb.pl[L - 1][c], od);
-          else ev = fma(t[v][c], tb.pl[L - 1][c], ev);
+          if (c & 1) od = fma_t(t[v][c], tb.pl[L - 1][c], od);
+          else ev = fma_t(t[v][c], tb.pl[L - 1][c], ev);
         }
         wp[v] = ev + od;
         wm[v] = ev - od;
         if (L == 3) {
-          double z = t[v][0] * tb.pl[1][0];
+          T z = t[v][0] * tb.pl[1][0];
 #pragma unroll
-          for (int c = 2; c <= N; c += 2) z = fma(t[v][c], tb.pl[1][c], z);
+          for (int c = 2; c <= N; c += 2) z = fma_t(t[v][c], tb.pl[1][c], z);
           w0[v] = z;
         }
       }
@@ -79,20 +90,20 @@ __device__ __forceinline__ void for_points(const double (*u)[np_of(DIM, N)], con
 #pragma unroll 1
       for (int i = 0; i < (kPair ? (N + 2) / 2 : N + 1); ++i) {
         const bool mid = !kPair || ((N % 2 == 0) && i == N / 2);  // one point (0 for N even)
-        double tp[V][N + 1], tm[V][N + 1];
+        T tp[V][N + 1], tm[V][N + 1];
 #pragma unroll
         for (int v = 0; v < V; ++v)
 #pragma unroll
           for (int c = 0; c <= N; ++c) {
-            double ev = 0.0, od = 0.0;
+            T ev = 0, od = 0;
 #pragma unroll
             for (int d = 0; d <= N - c; ++d) {
               const int m = pass == 0 ? mode_idx(d, c) : mode_idx(c, d);
               if (d & 1) {
-                if (!kPair) ev = fma(u[v][m], tb.pg[i][d], ev);
-                else if (!mid) od = d == 1 ? u[v][m] * tb.pg[i][d] : fma(u[v][m], tb.pg[i][d], od);
+                if (!kPair) ev = fma_t(u[v][m], tb.pg[i][d], ev);
+                else if (!mid) od = d == 1 ? u[v][m] * tb.pg[i][d] : fma_t(u[v][m], tb.pg[i][d], od);
               } else {
-                ev = d == 0 ? u[v][m] * tb.pg[i][d] : fma(u[v][m], tb.pg[i][d], ev);
+                ev = d == 0 ? u[v][m] * tb.pg[i][d] : fma_t(u[v][m], tb.pg[i][d], ev);
               }
             }
             const bool has_od = !mid && c < N;
@@ -141,25 +152,97 @@ __device__ __forceinline__ double pp_root(const double* ub, const double* uq, do
   return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
 }
 
-// counts[0] += cells changed, counts[1] += cells whose mean is not admissible.  The
-// density pass gives rho_min; the pressure pass evaluates every variable of the unscaled
-// state and applies the density factor to the density point values (rho' = rhobar +
-// theta1 (rho - rhobar), the point values of the scaled modes).
+// True when FP32 arithmetic with error margins proves that no check point of cell c needs
+// scaling: rho > eps and rho p > eps rho at every point, i.e. theta1 = theta2 = 1 and the
+// FP64 decisions below cannot fire.  With S_v = sum_k |U_vk| max|phi_k| (a bound on |u_v| at
+// every point) and delta = 2^-16 (over 16 times the error of truncating the modes to FP32
+// and of the FP32 sums), each point value is within delta S_v of the exact one, rho p
+// (times gamma - 1, minus eps rho) within 4 delta B, B = (gamma-1)(S_E S_rho + |S_m|^2) +
+// eps S_rho.  The caller requires rhobar, pbar >= 1e-10 and the bounds stay below 1e15, so
+// the margins are normal FP32 numbers; a NaN or infinity anywhere fails the test.
 template <int DIM, int N>
-__global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long long ctot, long long ncell,
-                                                    PpTab tb, unsigned long long* __restrict__ counts) {
+__device__ __forceinline__ bool screen_unchanged(const double* __restrict__ U, long long ctot, long long c,
+                                                 const PpTab& tb, float eps) {
+  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
+  constexpr float kDelta = 1.0f / 65536.0f;
+  float u[V][NP], S[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      u[v][k] = d2f_trunc(U[(long long)(v * NP + k) * ctot + c]);
+      const float phi = DIM == 1 ? tb.p1[k] : tb.p1[mode_a(k)] * tb.p1[mode_b(k)];
+      s = fmaf(fabsf(u[v][k]), phi, s);
+    }
+    S[v] = s;
+  }
+  float sm2 = S[1] * S[1];
+  if (V == 4) sm2 = fmaf(S[2], S[2], sm2);
+  const float gm1 = (float)tb.gm1;
+  const float B = fmaf(gm1, fmaf(S[V - 1], S[0], sm2), eps * S[0]);
+  if (!(B < 1e30f) || !(S[0] < 1e15f)) return false;
+  const float rho_min = fmaf(kDelta, S[0], eps), q_min = 4.0f * kDelta * B;
+  bool ok = true;
+  for_points<DIM, N, V>(u, tb.f, [&](const float* w) {
+    float k2 = w[1] * w[1];
+    if (V == 4) k2 = fmaf(w[2], w[2], k2);
+    const float q = fmaf(gm1, fmaf(w[V - 1], w[0], -0.5f * k2), -eps * w[0]);
+    ok &= (w[0] > rho_min) & (q > q_min);
+  });
+  return ok;
+}
+
+// First pass: lists the cells that the FP32 screen cannot prove unchanged (and those with
+// an inadmissible mean, which the second pass counts); warp ballot, one atomic per warp.
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) k_pp_screen(const double* __restrict__ U, long long ctot, long long ncell,
+                                                   PpTab tb, int* __restrict__ list, unsigned int* __restrict__ n_list) {
+  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
+  const int lane = threadIdx.x & 31;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
+    const long long c = base + threadIdx.x;
+    bool keep = false;
+    if (c < ncell) {
+      double ub[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) ub[v] = U[(long long)(v * NP) * ctot + c] * tb.c0;
+      const double pb = pp_pressure<V>(ub, tb.gm1);
+      if (!(ub[0] > 0.0) || !(pb > 0.0)) {
+        keep = true;
+      } else {
+        double eps = tb.eps0;
+        if (ub[0] < eps) eps = ub[0];
+        if (pb < eps) eps = pb;
+        keep = !(ub[0] >= 1e-10 && pb >= 1e-10 && screen_unchanged<DIM, N>(U, ctot, c, tb, (float)eps));
+      }
+    }
+    const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+    unsigned int pos0 = 0;
+    if (lane == 0 && bal) pos0 = atomicAdd(n_list, (unsigned)__popc(bal));
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    if (keep) list[pos0 + __popc(bal & ((1u << lane) - 1u))] = (int)c;
+  }
+}
+
+// Second pass, FP64, over the listed cells.  counts[0] += cells changed, counts[1] += cells
+// whose mean is not admissible.  The density pass gives rho_min; the pressure pass
+// evaluates every variable of the unscaled state and applies the density factor to the
+// density point values (rho' = rhobar + theta1 (rho - rhobar), the point values of the
+// scaled modes).
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long long ctot,
+                                                    const int* __restrict__ list,
+                                                    const unsigned int* __restrict__ n_list, PpTab tb,
+                                                    unsigned long long* __restrict__ counts) {
   constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
   unsigned int n_changed = 0, n_bad = 0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    double u[V][NP];
-#pragma unroll
-    for (int v = 0; v < V; ++v)
-#pragma unroll
-      for (int k = 0; k < NP; ++k) u[v][k] = U[(long long)(v * NP + k) * ctot + c];
+  const unsigned int nl = *n_list;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += gridDim.x * blockDim.x) {
+    const long long c = list[i];
     double ub[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) ub[v] = u[v][0] * tb.c0;
+    for (int v = 0; v < V; ++v) ub[v] = U[(long long)(v * NP) * ctot + c] * tb.c0;
     const double pb = pp_pressure<V>(ub, tb.gm1);
     if (!(ub[0] > 0.0) || !(pb > 0.0)) {
       ++n_bad;
@@ -168,6 +251,11 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
     double eps = tb.eps0;
     if (ub[0] < eps) eps = ub[0];
     if (pb < eps) eps = pb;
+    double u[V][NP];
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+      for (int k = 0; k < NP; ++k) u[v][k] = U[(long long)(v * NP + k) * ctot + c];
     // one pass for the density minimum and, assuming theta1 = 1 (the density needs no
     // scaling: the usual case), the pressure factor; with theta1 < 1 a second pass redoes
     // the pressure factor on the scaled density
@@ -273,9 +361,17 @@ static PpTab make_tab(int N, const double* pg, const double* pl, double c0, doub
   PpTab tb{};
   const int L = N == 1 ? 2 : 3;
   for (int i = 0; i <= N; ++i)
-    for (int k = 0; k <= N; ++k) tb.pg[i][k] = pg[i * (N + 1) + k];
+    for (int k = 0; k <= N; ++k) {
+      tb.pg[i][k] = pg[i * (N + 1) + k];
+      tb.f.pg[i][k] = (float)tb.pg[i][k];
+    }
   for (int j = 0; j < L; ++j)
-    for (int k = 0; k <= N; ++k) tb.pl[j][k] = pl[j * (N + 1) + k];
+    for (int k = 0; k <= N; ++k) {
+      tb.pl[j][k] = pl[j * (N + 1) + k];
+      tb.f.pl[j][k] = (float)tb.pl[j][k];
+    }
+  // psi_n(1) (the last Gauss-Lobatto point), rounded up so that S_v stays a bound
+  for (int k = 0; k <= N; ++k) tb.p1[k] = nextafterf((float)std::fabs(tb.pl[L - 1][k]), 1e30f);
   tb.c0 = c0;
   tb.gm1 = gam - 1.0;
   tb.eps0 = eps0;
@@ -300,11 +396,19 @@ void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long 
 #undef DG_SP
 }
 
+// list: int[ncell] scratch, n_list: its length (zeroed here)
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* pg, const double* pl, double c0, double gam, double eps0,
-                       unsigned long long* counts, int nblocks) {
+                       int* list, unsigned int* n_list, unsigned long long* counts, int nblocks) {
   const PpTab tb = make_tab(N, pg, pl, c0, gam, eps0);
-#define DG_PP(D, NN) k_positivity<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, ncell, tb, counts)
+  cudaMemsetAsync(n_list, 0, sizeof(unsigned int), st);
+  const long long want = (ncell + 255) / 256;
+  const int nb1 = (int)(want < 4LL * nblocks ? want : 4LL * nblocks);
+#define DG_PP(D, NN)                                                                                  \
+  do {                                                                                                \
+    k_pp_screen<D, NN><<<nb1, 256, 0, st>>>(U, ctot, ncell, tb, list, n_list);                        \
+    k_positivity<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, list, n_list, tb, counts);                  \
+  } while (0)
   if (dim == 1) {
     if (N == 1) DG_PP(1, 1);
     else if (N == 2) DG_PP(1, 2);

@@ -46,6 +46,46 @@ def test_positivity_limit_parity(dim, N, eps0):
     assert _rel(got, ref) <= 1e-12, _rel(got, ref)
 
 
+@pytest.mark.parametrize("dim,N", [(1, 2), (2, 2), (2, 3)])
+def test_fp32_screen_at_the_threshold(dim, N):
+    """Cells at rest whose smallest check-point density or pressure lies just below or just
+    above eps (relative offsets down to 1e-7, far inside the FP32 screen's margin yet
+    resolved by FP64) beside cells the screen clears: the screen may send a cell to the
+    FP64 pass but must never skip one that needs scaling, so the changed cells and the
+    scaled state equal the oracle's (unchanged cells bitwise)."""
+    eps0, gam = 1e-6, 1.4
+    offs = [-1e-3, -1e-5, -1e-7, 1e-7, 1e-5, 1e-3, 1.0, 1e3, 1e5]
+    ab = oracle.mode_ab(dim, N) if dim == 2 else [(k, 0) for k in range(N + 1)]
+    lin = ab.index((1, 0))  # linear in x: extreme at the check points x = -1, 1
+    psi0, psi1 = 1 / np.sqrt(2), np.sqrt(1.5)
+    c0 = psi0 * psi0 if dim == 2 else psi0  # cell mean = U_0 c0
+    k1 = psi1 * psi0 if dim == 2 else psi1  # |phi_lin| at x = -1, 1
+    E = dim + 1
+    cells = []
+    for var in (0, E):  # density, then energy (pressure (gamma - 1) E at rest)
+        for off in offs:
+            for mean in (1.0, 0.5):
+                u = np.zeros((dim + 2, len(ab)))
+                u[0, 0] = mean / c0
+                u[E, 0] = mean / (gam - 1) / c0
+                drop = mean - eps0 * (1 + off)  # the mean minus the smallest point value
+                u[var, lin] = drop / k1 if var == 0 else drop / ((gam - 1) * k1)
+                cells.append(u)
+    u = np.array(cells)
+    n = len(cells)
+    o = oracle.Mesh(dim, 1, N, n, 1, box=(0, 1, 0, 1), bc=1)
+    g = dgl.Mesh(dim, 1, N, [n], [1], [(0.0, 1.0, 0.0, 1.0)], bc=1)
+    g.set_modes(u)
+    g.positivity_limit(eps0)
+    got = g.get_modes()
+    ref, changed, bad = o.positivity_limit(u, eps0)
+    assert bad == 0 and g.positivity_counts() == (changed, 0)
+    assert changed == 2 * 2 * sum(1 for off in offs if off < 0), changed
+    unchanged = np.all(ref == u, axis=(1, 2))
+    assert np.array_equal(got[unchanged], u[unchanged])
+    assert _rel(got, ref) <= 1e-12
+
+
 def test_positivity_argument_errors():
     g = dgl.Mesh(1, 0, 2, [16], None, [(0.0, 1.0, 0.0, 1.0)])
     with pytest.raises(dgl.DGError):
@@ -79,7 +119,8 @@ def test_step_with_scaling_tube_p3_k800():
 def test_step_with_scaling_quadrant_p3():
     """2D Euler P3 four-quadrant problem (seed 31) on 38 x 38: the plain method reaches a
     negative pressure within 5 steps; with the scaling 30 steps stay admissible and match
-    the oracle step by step (CUDA graph path, three extra launches per step)."""
+    the oracle step by step (CUDA graph path, six extra launches per step: the FP32 screen
+    and the FP64 scaling after each stage)."""
     n = 38
     w = W.euler_2d_quadrant(n, 3, seed=31)
     o = oracle.Mesh(2, 1, 3, n, n, box=w.box[0], bc=w.bc)
@@ -99,7 +140,7 @@ def test_step_with_scaling_quadrant_p3():
     g.step(dt)
     g.set_positivity(False)
     g.step(dt)
-    assert g.launches - before == 2 * 18 + 3
+    assert g.launches - before == 2 * 18 + 6
 
 
 def _points(dim, N):
