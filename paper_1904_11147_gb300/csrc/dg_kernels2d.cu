@@ -36,9 +36,10 @@ struct Lay {
                                   2 * NG * N1 + 3 * NG;
   static constexpr int SIZE_PROJ = 3 * 8 + 8 * N1;
   static constexpr int SIZE_SPLIT = Q * N1;
-  static constexpr int SIZE_LIM2 = N1 * (N1 * (N1 + 1) / 2) + NG * N1;
+  static constexpr int SIZE_LIM2 = N1 * (N * N1 / 2) + NG * N1;
   static constexpr int SIZE_K = Q * N1 + N1;
-  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT + SIZE_LIM2 + SIZE_K;
+  static constexpr int SIZE_LIM3 = N1 * NG * N1;
+  static constexpr int SIZE = SIZE_DG + SIZE_FLAG + SIZE_LIM + SIZE_PROJ + SIZE_SPLIT + SIZE_LIM2 + SIZE_K + SIZE_LIM3;
 };
 __host__ __device__ constexpr int base_of(int N) {
   return N == 1 ? 0 : (N == 2 ? Lay<1>::SIZE : Lay<1>::SIZE + Lay<2>::SIZE);
@@ -74,11 +75,12 @@ struct Off {
   static constexpr int PQP = PW + 8;             // [8] (count in slot 0)
   static constexpr int PP = PQP + 8;             // [8][N1]
   static constexpr int WDQ = PP + 8 * N1;        // [Q][N1] w_q psi_n'(x_q)
-  static constexpr int BS = WDQ + Q * N1;        // [N1][k <= l] B_kk, B_kl + B_lk
-  static constexpr int WPG = BS + N1 * (N1 * (N1 + 1) / 2);  // [NG][N1] w_g psi_n(r_g)
+  static constexpr int BD = WDQ + Q * N1;        // [N1][j <= j'] Eq. (13) on differences (see pack)
+  static constexpr int WPG = BD + N1 * (N * N1 / 2);  // [NG][N1] w_g psi_n(r_g)
   static constexpr int KQ = WPG + NG * N1;       // [Q][N1] sqrt(2) psi_n(x_q) = psi_n(x_q) / psi_0
   static constexpr int KP1 = KQ + Q * N1;        // [N1] sqrt(2) psi_n(1)
-  static constexpr int END = KP1 + N1;
+  static constexpr int WCG = KP1 + N1;           // [N1 stencil][NG][N1] gamma_gi C_igk
+  static constexpr int END = WCG + N1 * NG * N1;
 };
 static_assert(Off<3>::END == Lay<1>::SIZE + Lay<2>::SIZE + Lay<3>::SIZE, "table layout");
 constexpr int kTabSize = Off<3>::END;
@@ -143,16 +145,30 @@ void pack(const dgt::Tabs& t, double* h) {
   h[O::PQP] = t.QP;
   for (int q = 0; q < Q; ++q)
     for (int n = 0; n < N1; ++n) h[O::WDQ + q * N1 + n] = t.gw[q] * t.dpsi_q[q][n];
-  for (int i = 0; i < N1; ++i) {
-    int j = 0;
-    for (int k = 0; k < N1; ++k)
-      for (int l = k; l < N1; ++l, ++j) h[O::BS + i * (N1 * (N1 + 1) / 2) + j] = k == l ? t.B[i][k][k] : t.B[i][k][l] + t.B[i][l][k];
-  }
   for (int g = 0; g < NG; ++g)
     for (int n = 0; n < N1; ++n) h[O::WPG + g * N1 + n] = t.rw[g] * t.psiG[g][n];
   for (int q = 0; q < Q; ++q)
     for (int n = 0; n < N1; ++n) h[O::KQ + q * N1 + n] = t.kq[q][n];
   for (int n = 0; n < N1; ++n) h[O::KP1 + n] = t.kp1[n];
+  // beta_i as a quadratic form in the N differences d_j = x_{i+j+1} - x_{i+j} of the
+  // stencil's averages x (beta ignores constants): with x_{i+k} - x_i = sum_{j<k} d_j,
+  // M_jj' = sum_{k > j, l > j'} B_ikl; packed as M_jj and M_jj' + M_j'j (j < j')
+  for (int i = 0; i < N1; ++i) {
+    int j = 0;
+    for (int a = 0; a < N; ++a)
+      for (int b = a; b < N; ++b, ++j) {
+        double mab = 0.0, mba = 0.0;
+        for (int k = a + 1; k < N1; ++k)
+          for (int l = b + 1; l < N1; ++l) {
+            mab += t.B[i][k][l];
+            mba += t.B[i][l][k];
+          }
+        h[O::BD + i * (N * N1 / 2) + j] = a == b ? mab : mab + mba;
+      }
+  }
+  for (int i = 0; i < N1; ++i)
+    for (int g = 0; g < NG; ++g)
+      for (int k = 0; k < N1; ++k) h[O::WCG + (i * NG + g) * N1 + k] = t.gam[g][i] * t.C[i][g][k];
 }
 
 // ----------------------------------------------------------------------------- loads
@@ -1115,54 +1131,62 @@ __global__ void __launch_bounds__(256)
 template <int N>
 __device__ __forceinline__ void weno(const double* avg, double* out) {
   using O = Off<N>;
-  constexpr int N1 = N + 1, NG = O::NG, NB = N1 * (N1 + 1) / 2;
+  constexpr int N1 = N + 1, NG = O::NG;
   const double eps = 1e-6;
-  // beta_i and p_i - c do not change when a constant c is removed from all averages
-  // (constants are reproduced; Eq. (13) holds only derivatives): work on averages
-  // centred at the troubled cell's own, which avoids cancellation in beta.
+  // p_i - c does not change when a constant c is removed from all averages (constants are
+  // reproduced): work on averages centred at the troubled cell's own
   const double c = avg[N];
   double dv[2 * N + 1];
 #pragma unroll
   for (int k = 0; k < 2 * N + 1; ++k) dv[k] = avg[k] - c;
-  // Eq. (13) as a symmetric quadratic form: beta_i = sum_k dv_k sum_{l >= k} Bs_kl dv_l;
+  // Eq. (13) holds only derivatives, so beta_i is a quadratic form in the differences of
+  // the stencil's averages: beta_i = sum_j df_{i+j} sum_{j' >= j} Md_jj' df_{i+j'};
   // inv_i = 1 / (eps + beta_i)^2
+  constexpr int ND = N * N1 / 2;
+  double df[2 * N];
+#pragma unroll
+  for (int k = 0; k < 2 * N; ++k) df[k] = avg[k + 1] - avg[k];
   double inv[N1];
 #pragma unroll
   for (int i = 0; i < N1; ++i) {
     double beta = 0.0;
     int j = 0;
 #pragma unroll
-    for (int k = 0; k < N1; ++k) {
-      double r = T(O::BS + i * NB + j) * dv[i + k];
+    for (int k = 0; k < N; ++k) {
+      double r = T(O::BD + i * ND + j) * df[i + k];
       ++j;
 #pragma unroll
-      for (int l = k + 1; l < N1; ++l, ++j) r = fma(T(O::BS + i * NB + j), dv[i + l], r);
-      beta = k == 0 ? dv[i] * r : fma(dv[i + k], r, beta);
+      for (int l = k + 1; l < N; ++l, ++j) r = fma(T(O::BD + i * ND + j), df[i + l], r);
+      beta = k == 0 ? df[i] * r : fma(df[i + k], r, beta);
     }
     const double d = eps + beta;
     inv[i] = rcp_d(d * d);
   }
-  // Eqs. (14)-(15): u_g = c + sum_i wbar_i (p_i - c) / sum_i wbar_i
+  // Eqs. (14)-(15): u_g = c + sum_i wbar_i (p_i - c) / sum_i wbar_i, wbar_i = gamma_gi inv_i;
+  // with the linear weights folded into the reconstruction tables (WCG = gamma_gi C_igk)
+  // the numerator is sum_i inv_i (gamma_gi (p_i - c))
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    double p[N1];
-#pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      double s = T(O::WC + (i * NG + g) * N1) * dv[i];
-#pragma unroll
-      for (int k = 1; k < N1; ++k) s = fma(T(O::WC + (i * NG + g) * N1 + k), dv[i + k], s);
-      p[i] = s;
-    }
     if (T(O::NEG + g) == 0.0) {
       double sw = 0.0, su = 0.0;
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
-        const double wb = T(O::GAM + g * N1 + i) * inv[i];
-        sw += wb;
-        su = fma(wb, p[i], su);
+        double s = T(O::WCG + (i * NG + g) * N1) * dv[i];
+#pragma unroll
+        for (int k = 1; k < N1; ++k) s = fma(T(O::WCG + (i * NG + g) * N1 + k), dv[i + k], s);
+        sw = i == 0 ? T(O::GAM + g * N1) * inv[0] : fma(T(O::GAM + g * N1 + i), inv[i], sw);
+        su = i == 0 ? inv[0] * s : fma(inv[i], s, su);
       }
       out[g] = fma(su, rcp_d(sw), c);
     } else {
+      double p[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        double s = T(O::WC + (i * NG + g) * N1) * dv[i];
+#pragma unroll
+        for (int k = 1; k < N1; ++k) s = fma(T(O::WC + (i * NG + g) * N1 + k), dv[i + k], s);
+        p[i] = s;
+      }
       double swp = 0.0, sup = 0.0, swm = 0.0, sum = 0.0;
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
@@ -1182,10 +1206,10 @@ __device__ __forceinline__ void weno(const double* avg, double* out) {
 // Right/left eigenvectors of the 2D Euler flux Jacobian in direction dir at state u.
 __device__ __forceinline__ void euler_eig2(const double* u, int dir, double gam, double (&R)[4][4],
                                            double (&L)[4][4]) {
-  const double rho = u[0], r = 1.0 / rho;
+  const double rho = u[0], r = rcp_d(rho);
   const double vx = u[1] * r, vy = u[2] * r, q2 = vx * vx + vy * vy;
   const double p = (gam - 1.0) * (u[3] - 0.5 * rho * q2);
-  const double c = sqrt(gam * p * r), ic = 1.0 / c;
+  const double c = sqrt_d(gam * p * r), ic = rcp_d(c);
   const double H = (u[3] + p) * r;
   const double b1 = (gam - 1.0) * ic * ic, b2 = 0.5 * b1 * q2;
   const double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
