@@ -514,7 +514,7 @@ def main():
     e2e_value = dofs * k_e2e * world / (e2e_ms / 1e3)
     flagged = lim_learned
 
-    # ------------------------------------------------------------ the judge (untimed)
+    # ------------------------------------------------------------ accuracy of the learned run (untimed)
     judge = missed = None
     if args.arms == "both" and rank == 0 and not args.no_judge:
         with torch.cuda.stream(st):
