@@ -83,7 +83,7 @@ void launch_kxrcf(int dim, int pde, int N, const LaunchArgs& a, const double* hp
                   int* lc, int* li);
 void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
                          const int* cell_inst, const double* pg, const double* pl, double gam, double* out,
-                         int nblocks);
+                         unsigned int* lb, int n_inst, int* list, unsigned int* n_list, int nblocks);
 void launch_positivity(int dim, int N, cudaStream_t st, double* U, long long ctot, long long ncell,
                        const double* pg, const double* pl, double c0, double gam, double eps0,
                        int* list, unsigned int* n_list, unsigned long long* counts, int nblocks);
@@ -204,8 +204,9 @@ struct dg_mesh {
   bool pp_on = false;
   double pp_eps0 = 1e-13;
   unsigned long long* pp_counts = nullptr;
-  int* pp_list = nullptr;          // Euler: cells the FP32 screen of the scaling leaves to FP64
+  int* pp_list = nullptr;          // Euler: cells an FP32 screen leaves to an FP64 pass
   unsigned int* pp_n = nullptr;
+  unsigned int* sp_lb = nullptr;   // Euler: [2 n_inst] lower bounds of the check-point wave speed
   bool g_pp = false;
   double g_pp_eps = 0.0;
   // KXRCF indicator: r^((N+1)/2) per instance (r the circumscribed radius) and the basis
@@ -251,7 +252,7 @@ extern "C" dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->d_bcd);
   cudaFree(m->lb_cell); cudaFree(m->lb_inst); cudaFree(m->lc_cell); cudaFree(m->lc_inst);
   cudaFree(m->cnt_b); cudaFree(m->cnt_c); cudaFree(m->fail); cudaFree(m->pos_counts);
-  cudaFree(m->pp_counts); cudaFree(m->pp_list); cudaFree(m->pp_n);
+  cudaFree(m->pp_counts); cudaFree(m->pp_list); cudaFree(m->pp_n); cudaFree(m->sp_lb);
   cudaFree(m->d_kx_hpow);
   delete m;
   return DG_OK;
@@ -395,7 +396,8 @@ extern "C" dg_status dg_mesh_create(int dim, int pde, int N, int n_inst, const i
             alloc((void**)&m->flag_totals, 3 * sizeof(unsigned long long)) &&
             alloc((void**)&m->pp_counts, 2 * sizeof(unsigned long long)) &&
             (pde != DG_EULER || (alloc((void**)&m->pp_list, sizeof(int) * off) &&
-                                 alloc((void**)&m->pp_n, sizeof(unsigned int)))) &&
+                                 alloc((void**)&m->pp_n, sizeof(unsigned int)) &&
+                                 alloc((void**)&m->sp_lb, sizeof(unsigned int) * 2 * n_inst))) &&
             alloc((void**)&m->d_kx_hpow, sizeof(double) * n_inst) &&
             (bc != DG_BC_DMR || alloc((void**)&m->d_bcd, sizeof(double) * (kDmrInst + kDmrStride * n_inst)));
   if (!ok) {
@@ -936,8 +938,8 @@ extern "C" dg_status dg_max_wavespeed_points(dg_mesh* m, double* out) {
   const long long want = (m->ncell + 127) / 128;
   const int nb = (int)std::max<long long>(1, std::min<long long>(want, (long long)m->sms * 16));
   launch_speed_points(m->dim, m->N, m->st, m->U[m->cur], m->ctot, m->ncell, m->d_cell_inst, m->pp_g, m->pp_l,
-                      m->gamma, m->d_speed, nb);
-  m->launches++;
+                      m->gamma, m->d_speed, m->sp_lb, m->n_inst, m->pp_list, m->pp_n, nb);
+  m->launches += 3;
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, m->d_speed, sizeof(double) * 2 * m->n_inst, cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));

@@ -304,20 +304,141 @@ __global__ void __launch_bounds__(128) k_positivity(double* __restrict__ U, long
   }
 }
 
-// Wave-speed bound over the check points of every cell, per instance and direction:
-// out[2 * inst + d] = max |v_d| + max c over the points (one square root per cell), the
-// non-negative doubles zeroed by the caller.  Points without a real sound speed are
-// skipped (a NaN never wins the comparison).
+// FP32 bounds of a cell's wave-speed bound max |v_d| + max c over its check points (the
+// FP64 value of k_speed_points): lo[d] <= it <= hi[d].  Point values carry the margins of
+// screen_unchanged (delta S_v); a point enters hi when its pressure may be >= 0 and lo only
+// when it surely is (the FP64 pass skips points without a real sound speed); a point whose
+// density may be <= 0 leaves hi unbounded.  The results are widened by 2^-12 (relative),
+// far more than the FP32 rounding of the bound formulas.
 template <int DIM, int N>
-__global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__ U, long long ctot, long long ncell,
+__device__ __forceinline__ void speed_bounds32(const double* __restrict__ U, long long ctot, long long c,
+                                               const PpTab& tb, float gam, float (&lo)[2], float (&hi)[2]) {
+  constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
+  constexpr float kDelta = 1.0f / 65536.0f;
+  const float kInf = __int_as_float(0x7f800000);
+  float u[V][NP], S[V];
+  bool unbounded = false;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    float sv = 0.f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      u[v][k] = d2f_trunc(U[(long long)(v * NP + k) * ctot + c]);
+      const float phi = DIM == 1 ? tb.p1[k] : tb.p1[mode_a(k)] * tb.p1[mode_b(k)];
+      sv = fmaf(fabsf(u[v][k]), phi, sv);
+    }
+    S[v] = kDelta * sv;
+    unbounded |= !(sv < 1e15f);
+  }
+  const float gm1 = gam - 1.0f;
+  float vlo[2] = {0.f, 0.f}, vhi[2] = {0.f, 0.f}, c2lo = 0.f, c2hi = 0.f;
+  for_points<DIM, N, V>(u, tb.f, [&](const float* w) {
+    const float rl = w[0] - S[0], ru = w[0] + S[0];
+    if (!(rl > 0.f)) {
+      unbounded = true;
+      return;
+    }
+    float ml[2] = {0.f, 0.f}, mu[2] = {0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      mu[d] = fabsf(w[1 + d]) + S[1 + d];
+      ml[d] = fmaxf(fabsf(w[1 + d]) - S[1 + d], 0.f);
+    }
+    const float m2l = fmaf(ml[1], ml[1], ml[0] * ml[0]), m2u = fmaf(mu[1], mu[1], mu[0] * mu[0]);
+    const float pu = gm1 * ((w[V - 1] + S[V - 1]) - 0.5f * m2l / ru);
+    const float pl = gm1 * ((w[V - 1] - S[V - 1]) - 0.5f * m2u / rl);
+    if (pu >= 0.f) {
+      c2hi = fmaxf(c2hi, gam * pu / rl);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) vhi[d] = fmaxf(vhi[d], mu[d] / rl);
+    }
+    if (pl > 0.f) {
+      c2lo = fmaxf(c2lo, gam * pl / ru);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) vlo[d] = fmaxf(vlo[d], ml[d] / ru);
+    }
+  });
+  const float cl = sqrtf(c2lo), ch = sqrtf(c2hi);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    lo[d] = (vlo[d] + cl) * (1.0f - 1.0f / 4096.0f);
+    hi[d] = unbounded ? kInf : (vhi[d] + ch) * (1.0f + 1.0f / 4096.0f);
+  }
+}
+
+// Pass 1: per instance and direction the largest lower bound over its cells (the float
+// bits of non-negative values order like unsigned integers); lb zeroed by the caller.
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) k_speed_lb(const double* __restrict__ U, long long ctot, long long ncell,
+                                                  const int* __restrict__ cell_inst, PpTab tb, float gam,
+                                                  unsigned int* __restrict__ lb) {
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
+    const long long c = base + threadIdx.x;
+    float lo[2] = {0.f, 0.f}, hi[2];
+    int inst = -1;
+    if (c < ncell) {
+      inst = cell_inst[c];
+      speed_bounds32<DIM, N>(U, ctot, c, tb, gam, lo, hi);
+    }
+    const int i0 = __shfl_sync(0xffffffffu, inst, 0);
+    const bool same = __all_sync(0xffffffffu, inst == i0 || inst < 0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      if (same) {
+        float m = lo[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && i0 >= 0) atomicMax(lb + 2 * i0 + d, __float_as_uint(m));
+      } else if (inst >= 0) {
+        atomicMax(lb + 2 * inst + d, __float_as_uint(lo[d]));
+      }
+    }
+  }
+}
+
+// Pass 2: lists the cells whose upper bound reaches their instance's largest lower bound in
+// some direction -- only these can hold the instance's maximum.
+template <int DIM, int N>
+__global__ void __launch_bounds__(256) k_speed_screen(const double* __restrict__ U, long long ctot, long long ncell,
+                                                      const int* __restrict__ cell_inst, PpTab tb, float gam,
+                                                      const unsigned int* __restrict__ lb, int* __restrict__ list,
+                                                      unsigned int* __restrict__ n_list) {
+  const int lane = threadIdx.x & 31;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
+    const long long c = base + threadIdx.x;
+    bool keep = false;
+    if (c < ncell) {
+      const int inst = cell_inst[c];
+      float lo[2], hi[2];
+      speed_bounds32<DIM, N>(U, ctot, c, tb, gam, lo, hi);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) keep |= !(hi[d] < __uint_as_float(lb[2 * inst + d]));
+    }
+    const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+    unsigned int pos0 = 0;
+    if (lane == 0 && bal) pos0 = atomicAdd(n_list, (unsigned)__popc(bal));
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    if (keep) list[pos0 + __popc(bal & ((1u << lane) - 1u))] = (int)c;
+  }
+}
+
+// Pass 3, FP64, over the listed cells: out[2 * inst + d] = max of max |v_d| + max c over the
+// check points (one square root per cell), the non-negative doubles zeroed by the caller.
+// Points without a real sound speed are skipped (a NaN never wins the comparison).
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) k_speed_points(const double* __restrict__ U, long long ctot,
+                                                      const int* __restrict__ list,
+                                                      const unsigned int* __restrict__ n_list,
                                                       const int* __restrict__ cell_inst, PpTab tb, double gam,
                                                       double* __restrict__ out) {
   constexpr int V = DIM == 1 ? 3 : 4, NP = np_of(DIM, N);
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < ncell; base += (long long)gridDim.x * blockDim.x) {
-    const long long c = base + threadIdx.x;
+  const unsigned int nl = *n_list;
+  for (unsigned int base = blockIdx.x * blockDim.x; base < nl; base += gridDim.x * blockDim.x) {
+    const unsigned int i = base + threadIdx.x;
     double sm[2] = {0.0, 0.0};
     int inst = -1;
-    if (c < ncell) {
+    if (i < nl) {
+      const long long c = list[i];
       inst = cell_inst[c];
       double u[V][NP];
 #pragma unroll
@@ -378,12 +499,24 @@ static PpTab make_tab(int N, const double* pg, const double* pl, double c0, doub
   return tb;
 }
 
-// pg: psi_n at the Gauss points [(N+1)][(N+1)], pl: at the Gauss-Lobatto points [L][(N+1)]
+// pg: psi_n at the Gauss points [(N+1)][(N+1)], pl: at the Gauss-Lobatto points [L][(N+1)];
+// lb: [2 n_inst] scratch, list: int[ncell] scratch, n_list: its length (both zeroed here);
+// out [2 n_inst] zeroed by the caller
 void launch_speed_points(int dim, int N, cudaStream_t st, const double* U, long long ctot, long long ncell,
                          const int* cell_inst, const double* pg, const double* pl, double gam, double* out,
-                         int nblocks) {
+                         unsigned int* lb, int n_inst, int* list, unsigned int* n_list, int nblocks) {
   const PpTab tb = make_tab(N, pg, pl, 0.0, gam, 0.0);
-#define DG_SP(D, NN) k_speed_points<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, ncell, cell_inst, tb, gam, out)
+  cudaMemsetAsync(lb, 0, sizeof(unsigned int) * 2 * n_inst, st);
+  cudaMemsetAsync(n_list, 0, sizeof(unsigned int), st);
+  const long long want = (ncell + 255) / 256;
+  const int nb1 = (int)(want < 4LL * nblocks ? want : 4LL * nblocks);
+  const float g32 = (float)gam;
+#define DG_SP(D, NN)                                                                                        \
+  do {                                                                                                      \
+    k_speed_lb<D, NN><<<nb1, 256, 0, st>>>(U, ctot, ncell, cell_inst, tb, g32, lb);                        \
+    k_speed_screen<D, NN><<<nb1, 256, 0, st>>>(U, ctot, ncell, cell_inst, tb, g32, lb, list, n_list);      \
+    k_speed_points<D, NN><<<nblocks, 128, 0, st>>>(U, ctot, list, n_list, cell_inst, tb, gam, out);        \
+  } while (0)
   if (dim == 1) {
     if (N == 1) DG_SP(1, 1);
     else if (N == 2) DG_SP(1, 2);
