@@ -132,6 +132,53 @@ def test_fallback_stage_by_stage_matches_oracle():
     assert seen_redo and seen_pass
 
 
+def test_fallback_with_positivity_scaling_matches_oracle():
+    """The same batch with the positivity-preserving scaling after every stage (the batched
+    P3 workload's setting): per instance and stage, the fallback decision on the skipped
+    cells, then the Zhang-Shu scaling of the result, against the oracle from the same input;
+    with the scaling on, no failure is counted."""
+    import torch
+    st = torch.cuda.Stream()
+    g, os_, us, dt = _mesh_and_state(st.cuda_stream)
+    net = dgl.MLP(dgl.n_features(2, 1, N), seed=5)
+    g.set_indicator(net, 1e30)  # keeps no cell
+    g.set_positivity(True, 1e-13)
+    sizes = [o.nx * o.ny for o in os_]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    prev = np.concatenate(us)
+    tot = 0
+    for k in range(3):
+        with torch.cuda.stream(st):
+            g.set_modes(prev)
+            fb0, _ = g.positivity_report()
+            g.step(dt, dgl.IND_MLP, 0.01)
+            got = g.get_modes()
+        fb1, fail1 = g.positivity_report()
+        redo = 0
+        for i, o in enumerate(os_):
+            sl = slice(offs[i], offs[i + 1])
+            u0 = prev[sl]
+            a = u0
+            for s in (1, 2, 3):
+                stg = o.rk_stage(s, dt, u0, a)
+                fl, _, _ = o.flag_tvb(stg, 0.01)
+                if fl.any():
+                    mg = _screen_margin(stg)[fl == 1]
+                    assert np.abs(mg[np.isfinite(mg)]).min() > 1e-5, "a screened point lies near the decision"
+                    if not (mg > 0).all():
+                        stg = o.limit(stg, fl)
+                        redo += 1
+                a, _, bad = o.positivity_limit(stg, 1e-13)
+                assert bad == 0
+            d, dh = rel(got[sl], a), rel_hi(got[sl], a)
+            assert d <= 1e-11 and dh <= 1e-11, (k, i, d, dh)
+        assert fb1 - fb0 == redo and fail1 == 0, (k, fb1 - fb0, redo, fail1)
+        tot += redo
+        prev = got
+    print("with the scaling: %d instance stages redone" % tot)
+    assert tot > 0
+
+
 def test_network_keeping_every_cell_is_the_plain_method():
     """tau below every logit: the learned indicator keeps every TVB-flagged cell, so a step
     equals the plain TVB step of the oracle (no cell is skipped, no fallback)."""
